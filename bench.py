@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Throughput of PERMANOVA's s_W on GB300: pair-permutation evaluations/s.
+
+A step is one permanova_sW call over one batch of label rows of the workload
+(all kernels of the path: label packing/validation, the dominant s_W kernel,
+the FP64 cross-tile reduction).  The default workload is n = 100,000 objects
+(Gaussian points in R^16, Euclidean fp32 distances, 40 GB), K = 10 groups with
+Dirichlet(2) sizes and 99,999 permutations in uint8 labels, processed in
+batches of 8,192 label rows per step; D (40 GB) is far larger than L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pair-perm evals/s for s_W at n=100k"
+UNIT = "pair-perm evals/s"
+WORKLOADS = {
+    "euclid-100k": dict(batch=8192),
+    "braycurtis-50k": dict(batch=8192),
+    "euclid-20k": dict(batch=4000),
+    "euclid-1k": dict(batch=1000),
+}
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(torch, dev: int) -> str | None:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        first = vis.split(",")[dev] if dev < len(vis.split(",")) else ""
+        return first or None
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: float) -> dict:
+    """Time the FP64 oracle (Algorithm 1) on the leading n_s x n_s block of
+    the workload with one label row per host thread; n_s is sized so the run
+    takes about ``target_s`` seconds."""
+    import oracle
+    T = oracle.max_threads()
+    K = cfg["K"]
+    w = cfg["w"].astype(np.float64)
+
+    ns = min(X.shape[0], 16384)
+    D = synth.euclidean_matrix(X[:ns]) if cfg["kind"] == "euclid" else \
+        synth.braycurtis_matrix(X[:ns])
+    pairs_s = ns * (ns - 1) / 2
+
+    def run(R: int) -> float:
+        rows = np.ascontiguousarray(np.resize(label_rows[:, :ns], (R, ns)).astype(np.int32) % K)
+        t0 = time.perf_counter()
+        oracle.sW_alg1(D, rows, K, w, threads=T)
+        return time.perf_counter() - t0
+
+    R = T
+    t = run(R)
+    rate = R * pairs_s / max(t, 1e-6)
+    if t < target_s / 3:
+        R = T * max(1, int(round(target_s * rate / pairs_s / T)))
+        R = min(R, 64 * T)
+        t = run(R)
+        rate = R * pairs_s / t
+    return {"value": rate, "unit": UNIT, "cores": T, "kind": "oracle",
+            "sample": f"FP64 Algorithm-1 oracle on the leading {ns}x{ns} block of the workload's "
+                      f"matrix with {R} label rows ({T} threads), {t:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+def roofline(form: str, K: int, evals_per_launch: float, kernel_ms: float, pk: dict,
+             traffic: float | None) -> dict:
+    s = kernel_ms / 1e3
+    if form == "gemm":
+        flops = 4.0 * K * evals_per_launch          # two BF16 planes x 2K flops per pair-perm
+        achieved = flops / s / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": pk["source"] + " (sustained bf16)"}
+    if form == "permblock":
+        ops = 2.0 * evals_per_launch                 # one compare + one add per pair-perm
+        achieved = ops / s / 1e12
+        peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+    byts = 4.0 * evals_per_launch                    # fp32 d_ij re-read per label row
+    achieved = byts / s / 1e9
+    peak = pk["hbm_gbs"]
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"] + " (copy)"}
+
+
+def traffic_per_launch(form: str, evals: float) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (bytes per pair-perm evaluation x evaluations)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = {"gemm": "k_gemm.cu", "permblock": "k_permblock.cu", "brute": "k_brute.cu"}[form]
+    with open(os.path.join(ROOT, "paper_2505_04556_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()[:12]
+    for line in open(path):
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("form") == form and kv.get("src_sha") == sha and "bytes_per_eval" in kv:
+            return float(kv["bytes_per_eval"]) * evals
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="euclid-100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--form", default="auto", choices=["auto", "brute", "permblock", "gemm"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cfg = synth.recipe(args.workload)
+    B = args.batch or WORKLOADS[args.workload]["batch"]
+    B = min(B, cfg["P"])
+    n, K, P = cfg["n"], cfg["K"], cfg["P"]
+    pairs = n * (n - 1) / 2
+    X = synth.recipe_points(cfg)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # every step: the oracle on a bounded sample of the same workload
+        rows = synth.shuffled_rows(cfg["labels"], 64, cfg["seed_perms"])
+        per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+        first = oracle_rate(cfg, X, rows, per_step)
+        rates = []
+        for k in range(args.steps + args.warmup - 1):
+            r = oracle_rate(cfg, X, rows, per_step)
+            if k >= args.warmup - 1:
+                rates.append(r["value"])
+        if not rates:
+            rates = [first["value"]]
+        value = statistics.median(rates)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "K": K, "P_total": P,
+                           "label_type": cfg["label_type"],
+                           "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": first["cores"],
+                                 "kind": "oracle", "sample": first["sample"]},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import paper_2505_04556_gb300 as pm
+
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    pm.build()
+    ctx = pm.Context(dev)
+    form_id = {"auto": pm.FORM_AUTO, "brute": pm.FORM_BRUTE, "permblock": pm.FORM_PERMBLOCK,
+               "gemm": pm.FORM_GEMM}[args.form]
+    ctx.set_form(form_id)
+    form = pm.FORM_NAMES[pm.permanova_plan_form(ctx.handle, n, K, B)]
+
+    # ---- inputs resident in HBM before timing ----
+    D = synth.recipe_matrix_device(cfg, X, device=f"cuda:{dev}")
+    n_rows = min(P, (args.warmup + args.steps) * B)
+    lab = synth.device_label_rows(cfg["labels"], n_rows, cfg["seed_perms"] + 1000 * rank,
+                                  device=f"cuda:{dev}", dtype=torch.uint8)
+    w = torch.from_numpy(cfg["w"]).to(f"cuda:{dev}")
+    out = torch.empty(n_rows, dtype=torch.float64, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k: int):
+        b0 = (k * B) % n_rows
+        bb = min(B, n_rows - b0)
+        pm.permanova_sW(ctx.handle, D, n, D.stride(0), lab[b0:b0 + bb], pm.LABEL_U8, K, bb, w,
+                        out[b0:b0 + bb], stream)
+        return bb
+
+    for k in range(args.warmup):
+        step(k)
+    pm.permanova_sync(ctx.handle, stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(gpu_query_id(torch, dev))
+    pm.permanova_profile_enable(ctx.handle, True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    rows_done = 0
+    for k in range(args.steps):
+        rows_done += step(args.warmup + k)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    prof = pm.permanova_profile_read(ctx.handle)
+    pm.permanova_profile_enable(ctx.handle, False)
+    pm.permanova_sync(ctx.handle, stream)
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        import torch.distributed as dist
+        tms = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
+        ms = float(tms.item())
+        rd = torch.tensor([rows_done], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(rd, op=dist.ReduceOp.SUM)
+        rows_total = float(rd.item())
+    else:
+        rows_total = float(rows_done)
+    value = pairs * rows_total / (ms / 1e3)
+
+    # ---- dominant kernel roofline ----
+    launches = max(1, prof["main_kernel_launches"])
+    kernel_ms = prof["main_kernel_ms"] / launches
+    evals_per_launch = pairs * rows_done / launches
+    pk = peaks()
+    rl = roofline(form, K, evals_per_launch, kernel_ms, pk,
+                  traffic_per_launch(form, evals_per_launch))
+    rl["kernel_ms"] = kernel_ms
+
+    # ---- end to end through the host entry point ----
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        Dh.copy_(D)
+        labh = torch.empty((B, n), dtype=torch.uint8, pin_memory=True)
+        labh.copy_(lab[:B])
+        wh = torch.from_numpy(cfg["w"].copy())
+        outh = torch.empty(B, dtype=torch.float64, pin_memory=True)
+        del D
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            pm.permanova_sW_host(ctx.handle, Dh, n, n, labh, pm.LABEL_U8, K, B, wh, outh, stream)
+            return float(outh[0])
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": pairs * B * args.e2e_steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * n * 4 + B * n + K * 4),
+               "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps,
+               "api": "permanova_sW_host (pinned host D, labels, weights, results)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rows_h = lab[:64].cpu().numpy() if not args.no_e2e else labh[:64].numpy()
+        cpu = oracle_rate(cfg, X, rows_h, 15.0)
+
+    if rank == 0:
+        dtype = "bf16 hi+lo, f32 accumulate" if form == "gemm" else "f32"
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": dtype, "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "K": K, "P_total": P,
+                           "batch": B, "label_type": "u8", "form": form,
+                           "matrix": "Gaussian points in R^16 (group shift 0.3 sd), Euclidean fp32"
+                           if cfg["kind"] == "euclid" else "Dirichlet(0.5) x 200, Bray-Curtis fp32",
+                           "l2": f"inputs larger than L2 (D = {n * n * 4 / 1e9:.1f} GB)",
+                           "parallelism": f"replicas x{world} (label rows split)"},
+                "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(prof["kernel_launches"]),
+                "gpu": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * permanova.h -- C ABI of libpermanova.so, PERMANOVA's within-group statistic
+ * s_W on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the one the paper calls permanova_f_stat_sW ("Comparing CPU
+ * and GPU compute of PERMANOVA on MI300A", Sec. 2, Algorithms 1-3): for each
+ * label row p of a batch of groupings,
+ *
+ *     s_W[p] = sum over 0 <= i < j < n with g_p(i) == g_p(j) of
+ *              mat[i*ld + j]^2 * inv_group_sizes[g_p(i)]
+ *
+ * over a dense distance matrix of which only the strict upper triangle
+ * (column > row) is read; the diagonal and the lower triangle may hold
+ * anything, NaN included.  Around it, permanova_test adds the steps the paper
+ * places "before and after" s_W (Sec. 2) for the permutation test of Sec. 1:
+ * group sizes, permutations of the observed grouping, the total sum of squares
+ * s_T, the pseudo-F statistic and the permutation p-value.
+ *
+ * Conventions for every call:
+ *  - Every function returns a permanova_status (0 = success).  On failure a
+ *    message is available from permanova_last_error(ctx) until the next call
+ *    on the same context from the same thread.
+ *  - "DEVICE" pointers are CUDA device (or managed) memory on the context's
+ *    device; "HOST" pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes; the library never frees or retains them after the call.
+ *  - Scratch memory (partial sums, packed labels, the split D^2 planes of the
+ *    tensor-core form, permutation labels) belongs to the context, is reused
+ *    across calls and is bounded by the context's HBM budget: a call whose
+ *    scratch would exceed the budget returns PERMANOVA_ENOMEM before
+ *    allocating anything.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Asynchronous calls only enqueue work on it.
+ *  - Calls on one context are serialised by an internal lock; separate
+ *    contexts are independent.
+ *  - Device kernels never trap.  A label found outside [0, n_groups) or a
+ *    device-side wait that ran out of time sets a device error word; the next
+ *    call that synchronises (permanova_sync, permanova_test, the _host
+ *    variants) returns PERMANOVA_EINVAL / PERMANOVA_ETIMEOUT and clears it.
+ *    The outputs of the failed batch are unspecified.
+ */
+#ifndef PERMANOVA_H
+#define PERMANOVA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PERMANOVA_OK = 0,
+    PERMANOVA_EINVAL = 1,       /* bad argument, or a label >= n_groups found on the device */
+    PERMANOVA_ENOMEM = 2,       /* scratch would exceed the HBM budget, or cudaMalloc failed */
+    PERMANOVA_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    PERMANOVA_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    PERMANOVA_EUNSUPPORTED = 5  /* form not available for these sizes (e.g. GEMM with K > 256) */
+} permanova_status;
+
+/* Element type of the label rows ("groupings").  The paper's listings use
+ * int; the packed types cut label traffic 4x / 2x. */
+typedef enum {
+    PERMANOVA_LABEL_I32 = 0,
+    PERMANOVA_LABEL_U16 = 1,
+    PERMANOVA_LABEL_U8 = 2
+} permanova_label_t;
+
+/* Kernel form used for s_W.
+ *   BRUTE      Algorithm 3's brute force: the triangle is streamed from HBM
+ *              once per label row (HBM-bound).
+ *   PERMBLOCK  a triangle tile of D^2 is held in shared memory and reused by
+ *              a block of 128 label rows (CUDA-core, issue-bound); the row
+ *              weight is applied once per row segment as in Algorithm 2.
+ *   GEMM       the dense-contraction form Z_p = (D o D) X_p with one-hot
+ *              indicator columns X_p, on the tcgen05 tensor cores: D^2 split
+ *              into BF16 hi + lo, FP32 accumulation in tensor memory, FP64
+ *              partial sums.  Needs n_groups <= 256.
+ *   AUTO       the planner's choice for (n, K, P). */
+typedef enum {
+    PERMANOVA_FORM_AUTO = 0,
+    PERMANOVA_FORM_BRUTE = 1,
+    PERMANOVA_FORM_PERMBLOCK = 2,
+    PERMANOVA_FORM_GEMM = 3
+} permanova_form_t;
+
+typedef struct permanova_ctx permanova_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * context's scratch (0 = 90% of the device's free memory at creation).
+ * *out receives the context; NULL on failure.  Returns EINVAL for a bad
+ * device or NULL out, ECUDA if the device cannot be initialised. */
+int permanova_create(int device, size_t hbm_budget_bytes, permanova_ctx **out);
+
+/* Synchronise the context's device, free its scratch and destroy it.  NULL is
+ * a no-op. */
+void permanova_destroy(permanova_ctx *ctx);
+
+/* Message describing the last failure on this thread for ctx ("" if none).
+ * The pointer stays valid until the next call on ctx from this thread. */
+const char *permanova_last_error(const permanova_ctx *ctx);
+
+/* Force a kernel form for subsequent calls (PERMANOVA_FORM_AUTO restores the
+ * planner).  Returns EINVAL for an unknown form. */
+int permanova_set_form(permanova_ctx *ctx, int form);
+
+/* Form the planner would use (or the forced one) for these sizes. */
+int permanova_plan_form(permanova_ctx *ctx, uint32_t n_dims, uint32_t n_groups, uint64_t n_perms);
+
+/* Bytes of context scratch a permanova_sW call of these sizes needs under
+ * `form` (AUTO = the planner's form).  0 on invalid sizes. */
+size_t permanova_scratch_bytes(permanova_ctx *ctx, int form, uint32_t n_dims, uint32_t n_groups,
+                               uint64_t n_perms);
+
+/* The paper's permanova_f_stat_sW_T (Sec. 2, Algorithm 1's driver): s_W for
+ * n_perms label rows.  Asynchronous on `stream`.
+ *   mat              DEVICE, fp32, row-major, n_dims rows of stride ld
+ *                    elements (ld >= n_dims); only column > row is read.
+ *   groupings        DEVICE, n_perms rows of n_dims labels, perm-major: label
+ *                    of object i in row p at groupings[p*n_dims + i], element
+ *                    type label_type; every label must be < n_groups.
+ *   inv_group_sizes  DEVICE, n_groups fp32 weights (the paper's
+ *                    inv_group_sizes; normally 1/n_g, any value accepted).
+ *   out_sW           DEVICE, n_perms doubles, written in full.
+ * Errors: EINVAL for NULL pointers, n_dims < 2, ld < n_dims, n_groups == 0,
+ * n_groups > 256 with U8 or > 65536 with U16, n_perms == 0; ENOMEM if the
+ * scratch exceeds the budget; EUNSUPPORTED if a forced form cannot run these
+ * sizes; ECUDA on a launch failure.  Labels >= n_groups are reported by the
+ * next synchronising call. */
+int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                 const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
+                 const float *inv_group_sizes, double *out_sW, void *stream);
+
+/* Same as permanova_sW with HOST buffers: mat (n_dims x ld fp32),
+ * groupings, inv_group_sizes and out_sW live in host memory (pinned memory
+ * gives full copy speed).  The call copies the inputs to the device, runs
+ * s_W, copies the n_perms results back and synchronises `stream`. */
+int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                      const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
+                      const float *inv_group_sizes, double *out_sW, void *stream);
+
+/* Wait for `stream`, then report (and clear) any device error word raised by
+ * earlier asynchronous calls on this context.  Returns OK, EINVAL (invalid
+ * label), ETIMEOUT or ECUDA. */
+int permanova_sync(permanova_ctx *ctx, void *stream);
+
+/* Permutation labels for the test of Sec. 1 ("assignment of objects to
+ * groups randomly permuted"), generated on the device:
+ *   grouping   DEVICE, n_dims int32 observed labels in [0, n_groups).
+ *   out        DEVICE, (n_perms + 1) rows of n_dims labels of label_type;
+ *              row 0 = grouping, row p >= 1 = an independent Fisher-Yates
+ *              shuffle of grouping driven by Philox4x32-10 (Salmon et al.,
+ *              SC'11) under key (seed mod 2^32, seed / 2^32) and counter
+ *              (block, 0, p, 0), words taken in order, bounded draws by
+ *              Lemire's multiply-shift with rejection.
+ * Asynchronous.  EINVAL for NULL pointers, n_dims < 2, n_perms == 0 or
+ * n_perms >= 2^32 - 1, n_dims >= 2^32, a label type too narrow for
+ * n_groups. */
+int permanova_permutations(permanova_ctx *ctx, const int32_t *grouping, uint32_t n_dims,
+                           uint32_t n_groups, uint64_t n_perms, uint64_t seed, void *out,
+                           int label_type, void *stream);
+
+/* Profiling counters of a context (not a paper operation; measurement
+ * support).  While enabled, every s_W call records CUDA events on its stream
+ * around its dominant kernel (the brute-force, perm-block or GEMM kernel) and
+ * every kernel the library launches is counted. */
+typedef struct {
+    double main_kernel_ms;          /* summed event time of the dominant kernels */
+    uint64_t main_kernel_launches;  /* dominant-kernel launches recorded */
+    uint64_t kernel_launches;       /* all kernels launched by the library */
+    int last_form;                  /* permanova_form_t of the last s_W call */
+} permanova_profile_t;
+
+/* Enable (1) or disable (0) profiling; enabling clears the counters. */
+int permanova_profile_enable(permanova_ctx *ctx, int enable);
+
+/* Synchronise the context's device, sum the recorded events into *out
+ * (HOST) and clear the counters. */
+int permanova_profile_read(permanova_ctx *ctx, permanova_profile_t *out);
+
+typedef struct {
+    double s_T;        /* (1/n) sum_{i<j} d_ij^2 */
+    double s_W_obs;    /* s_W of the observed grouping */
+    double F_obs;      /* ((s_T - s_W)/(K-1)) / (s_W/(n-K)) */
+    double p_value;    /* (1 + n_ge) / (1 + n_perms) */
+    uint64_t n_ge;     /* #{p >= 1 : F_p >= F_obs}, counted as s_W[p] <= s_W_obs */
+    uint64_t n_perms;  /* permutations drawn */
+} permanova_result;
+
+/* One PERMANOVA test (Sec. 1; s_W as in Sec. 2).
+ *   mat        DEVICE distance matrix as in permanova_sW.
+ *   grouping   DEVICE, n_dims int32 labels in [0, n_groups), every group
+ *              non-empty.
+ *   n_perms    permutations (>= 1); their labels come from
+ *              permanova_permutations with `seed`.
+ *   out_host   HOST, receives the result.
+ *   out_sW     optional DEVICE buffer of n_perms + 1 doubles (NULL = none):
+ *              s_W of the observed grouping (index 0) and of every
+ *              permutation.
+ * Synchronises `stream`.  EINVAL for NULL mat/grouping/out_host, n_groups < 2,
+ * n_dims <= n_groups (pseudo-F undefined), an empty group or a label outside
+ * [0, n_groups); plus the errors of permanova_sW. */
+int permanova_test(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                   const int32_t *grouping, uint32_t n_groups, uint64_t n_perms, uint64_t seed,
+                   permanova_result *out_host, double *out_sW, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERMANOVA_H */

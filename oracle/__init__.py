@@ -84,9 +84,15 @@ def _ptr(a: np.ndarray):
 
 
 def _mat(mat) -> tuple[np.ndarray, int, int]:
-    m = np.ascontiguousarray(mat, dtype=np.float32)
+    """(array, n, ld): a square float32 matrix; a row-strided view (e.g. the
+    leading block of a larger matrix) is passed with its row stride, uncopied."""
+    m = np.asarray(mat)
     if m.ndim != 2 or m.shape[0] != m.shape[1]:
         raise ValueError("distance matrix must be square")
+    if (m.dtype == np.float32 and m.strides[1] == 4 and m.strides[0] % 4 == 0
+            and m.strides[0] >= 4 * m.shape[1]):
+        return m, m.shape[0], m.strides[0] // 4
+    m = np.ascontiguousarray(m, dtype=np.float32)
     return m, m.shape[0], m.shape[1]
 
 

@@ -1,0 +1,134 @@
+// Device-side helpers shared by the s_W kernels of libpermanova.
+//
+// Label element types (int32 / uint16 / uint8, perm-major rows as in the
+// paper's Algorithm 1 driver: labels of row p at groupings + p*n), the
+// device error word, and the launch prototypes the host runtime calls.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pmn {
+
+// Device error word.  Kernels never trap: they record the first problem here
+// and the host reports it at the next synchronising call.
+struct DevStatus {
+    unsigned int code;       // 0 = ok, see DEV_* below
+    unsigned int where;      // kernel-specific detail (row, stage, ...)
+    unsigned long long info; // e.g. flat index of a bad label
+};
+enum : unsigned int { DEV_OK = 0, DEV_BAD_LABEL = 1, DEV_TIMEOUT = 2 };
+
+enum LabelType : int { LABEL_I32 = 0, LABEL_U16 = 1, LABEL_U8 = 2 };
+
+template <typename L>
+__device__ __forceinline__ uint32_t label_at(const L* __restrict__ p, uint64_t idx) {
+    return (uint32_t)__ldg(p + idx);
+}
+
+__device__ __forceinline__ void raise_status(DevStatus* st, unsigned int code, unsigned int where,
+                                             unsigned long long info) {
+    if (atomicCAS(&st->code, 0u, code) == 0u) {
+        st->where = where;
+        st->info = info;
+    }
+}
+
+// Number of strict-upper-triangle pairs in rows [0, r) of an n x n matrix.
+__host__ __device__ __forceinline__ uint64_t pairs_before_row(uint64_t r, uint64_t n) {
+    return r * n - r * (r + 1) / 2;
+}
+
+// First row r with pairs_before_row(r) >= target (0 <= target <= total).
+__host__ __device__ __forceinline__ uint32_t row_for_pair(uint64_t target, uint32_t n) {
+    uint32_t lo = 0, hi = n;  // answer in [lo, hi]
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (pairs_before_row(mid, n) >= target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+struct SWProblem {
+    const float* mat;
+    uint32_t n;
+    uint64_t ld;
+    const void* labels;
+    int label_type;
+    uint32_t K;
+    uint64_t P;
+    const double* w;   // inv_group_sizes widened to FP64 (device)
+    double* out;
+};
+
+// inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
+cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t s);
+
+// Count of kernels the library has launched (all contexts); launchers return
+// launched(k) after issuing k kernels.
+void note_launches(unsigned k);
+uint64_t kernel_launch_count();
+inline cudaError_t launched(unsigned k) {
+    note_launches(k);
+    return cudaGetLastError();
+}
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_validate_labels(const void* labels, int type, uint64_t count, uint32_t K,
+                                   DevStatus* st, cudaStream_t s);
+cudaError_t launch_reduce_rows(const double* partials, uint32_t rows, uint64_t P, double* out,
+                               cudaStream_t s);
+cudaError_t launch_fill_u8(uint8_t* p, uint64_t count, uint8_t v, cudaStream_t s);
+
+// brute force (Algorithm 3 semantics): partials is n_chunks x P
+uint32_t brute_chunks(uint32_t n, int sm_count);
+cudaError_t launch_brute(const SWProblem& pr, uint32_t n_chunks, double* partials,
+                         const DevStatus* st, cudaStream_t s);
+// sum of squares of the strict upper triangle: partials is n_chunks x 1
+cudaError_t launch_sumsq_triangle(const float* mat, uint32_t n, uint64_t ld, uint32_t n_chunks,
+                                  double* partials, cudaStream_t s);
+
+// perm-block CUDA-core form: partials is permblock_bands(n) x P; labels are
+// uint8/uint16 codes with a 16-byte-multiple row stride of lstride elements
+uint32_t permblock_bands(uint32_t n);
+cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
+                                      const DevStatus* st, cudaStream_t s);
+
+// labels -> uint8/uint16 codes with row stride lstride (padding = 0); labels
+// >= K raise DEV_BAD_LABEL and are clamped to K-1
+cudaError_t launch_repack_labels(const void* in, int in_type, uint32_t n, uint64_t P, uint32_t K,
+                                 void* out, int out_type, uint64_t lstride, DevStatus* st,
+                                 cudaStream_t s);
+
+// tcgen05 GEMM form
+struct GemmPlan {
+    uint32_t n_pad;        // n rounded up to 128
+    uint32_t n_bands;      // n_pad / 128
+    uint32_t perms_per_tile;
+    uint64_t n_ptiles;
+    uint64_t plane_elems;  // bf16 elements per plane (hi or lo) of the banded upper triangle
+};
+bool gemm_available();
+GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P);
+size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t P);
+// D^2 -> BF16 hi/lo operand tiles in the scratch
+cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s);
+// the tensor-core kernel: partials is gp.n_bands x P
+cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
+                             double* partials, DevStatus* st, int sm_count, cudaStream_t s);
+
+// permutation test helpers
+cudaError_t launch_permutations(const int32_t* grouping, uint32_t n, uint64_t n_perms,
+                                uint64_t seed, void* out, int label_type, cudaStream_t s);
+struct TestScalars {
+    double s_T;
+    double s_W_obs;
+    double F_obs;
+    double p_value;
+    unsigned long long n_ge;
+    unsigned long long n_perms;
+};
+cudaError_t launch_finalize(const double* sW, uint64_t n_perms, const double* sT_sum, uint32_t n,
+                            uint32_t K, TestScalars* out, cudaStream_t s);
+
+}  // namespace pmn

@@ -1,0 +1,583 @@
+// Tensor-core (tcgen05 / TMEM) form of s_W.
+//
+// Algebra.  Algorithm 1 (Sec. 2) sums d_ij^2 * w_{g_p(i)} over pairs i < j
+// with g_p(i) == g_p(j).  With M = the strict upper triangle of D o D and the
+// one-hot indicator X_p (n x K, X_p[j, g] = [g_p(j) == g]),
+//     Z_p = M X_p,   s_W[p] = sum_i w_{g_p(i)} Z_p[i, g_p(i)],
+// so the pair sum becomes a dense contraction over j, one GEMM column per
+// (label row, group).  This costs K times the useful work of the brute force
+// but runs on the tensor cores.
+//
+// Precision.  d^2 is formed in FP32 and split into two BF16 planes,
+// hi = bf16(d^2), lo = bf16(d^2 - hi) (the difference is exact in FP32), so
+// hi + lo carries 16 significant bits (relative error <= 2^-17 per term); the
+// one-hot operand is exact in BF16.  Both planes multiply the same B operand
+// into one FP32 accumulator in tensor memory.  The accumulator is drained
+// every DRAIN_KB k-blocks (1,024 columns); the drained row values are
+// weighted in FP64, reduced over the 128 rows in a fixed order and
+// accumulated in FP64.
+//
+// Layout.  A prep kernel writes, for every 128-row band I and 64-column
+// k-block kb >= 2I of the triangle, one 32 KB tile: the hi plane (128 x 64
+// BF16) then the lo plane, each already in the tensor core's K-major 128-byte
+// swizzled layout, so one bulk copy (TMA engine) moves both planes.  Entries
+// with j <= i, i >= n or j >= n are zero.
+//
+// Kernel.  Persistent, one CTA per SM, 12 warps:
+//   warp 0       bulk-copies the A tiles and the 64-column label slices of the
+//                tile's label rows into a 3-stage shared-memory ring;
+//   warp 1       owns 512 TMEM columns (two 128 x 256 FP32 accumulators) and
+//                issues the tcgen05.mma instructions (one thread);
+//   warps 4-7    drain the accumulators (tcgen05.ld), keep column
+//                (p, g_p(i)) of each row, weight it, reduce over rows;
+//   warps 8-11   build the one-hot B tile of each stage from the labels.
+// Work unit = (band I, tile of up to 64 label rows), band-major so the CTAs
+// running together share a band and read its A tiles from L2.
+// Every wait is bounded; on timeout the kernel records DEV_TIMEOUT, lets the
+// other roles run out, waits for its own copies and MMAs, frees its TMEM and
+// returns.
+#include "common.cuh"
+
+#include <cuda_bf16.h>
+
+namespace pmn {
+
+namespace g {
+constexpr int BM = 128;             // band height (MMA M)
+constexpr int BK = 64;              // k-block width (one 128-byte swizzle atom of BF16)
+constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
+constexpr int PPT_MAX = 64;         // label rows per tile
+constexpr int NST = 3;              // pipeline stages
+constexpr int DRAIN_KB = 16;        // k-blocks per accumulator chunk
+constexpr int THREADS = 384;
+constexpr uint32_t PLANE_BYTES = BM * BK * 2;             // 16 KB
+constexpr uint32_t TILE_BYTES = 2 * PLANE_BYTES;          // hi + lo planes: 32 KB
+constexpr uint32_t A_BYTES = TILE_BYTES;
+constexpr uint32_t B_BYTES = NMAX * BK * 2;               // 32 KB
+constexpr uint32_t LAB_BYTES = PPT_MAX * BK;              // 4 KB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES + LAB_BYTES;   // 68 KB
+constexpr uint32_t OFF_LABROWS = NST * STAGE_BYTES;
+constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][PPT_MAX] double
+constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * PPT_MAX * 8;
+constexpr uint32_t OFF_W = OFF_ACC64 + PPT_MAX * 8;               // [256] double
+constexpr uint32_t OFF_BAR = OFF_W + 256 * 8;
+constexpr uint32_t N_BARS = 3 * NST + 6;
+constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
+constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
+constexpr uint32_t SMEM_ALLOC = SMEM_BYTES + 1024;       // room to align the base to 1 KB
+constexpr long long WAIT_LIMIT = 4000000000LL;           // clock cycles (~2 s)
+static_assert(SMEM_ALLOC <= 232448, "shared memory budget");
+}  // namespace g
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core-matrix groups 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address
+    d |= (uint64_t)1u << 16;                       // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: 1024 B
+    d |= (uint64_t)1u << 46;                       // version
+    d |= (uint64_t)2u << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Byte offset of 16-byte chunk c (0..7) of row r inside a K-major 128-byte
+// swizzled tile (rows of 128 bytes, 8-row atoms of 1024 bytes).
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t c) {
+    return (r >> 3) * 1024u + (r & 7u) * 128u + ((c ^ (r & 7u)) << 4);
+}
+
+// ---------------------------------------------------------------------------
+// plan and scratch
+// ---------------------------------------------------------------------------
+bool gemm_available() { return true; }
+
+GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P) {
+    GemmPlan gp{};
+    gp.n_pad = (n + g::BM - 1) / g::BM * g::BM;
+    gp.n_bands = gp.n_pad / g::BM;
+    uint32_t ppt = K ? g::NMAX / K : 0;
+    if (ppt > (uint32_t)g::PPT_MAX) ppt = g::PPT_MAX;
+    gp.perms_per_tile = ppt;
+    gp.n_ptiles = ppt ? (P + ppt - 1) / ppt : 0;
+    const uint64_t nb = gp.n_bands;
+    gp.plane_elems = nb * (nb + 1) * (uint64_t)g::BM * g::BK;  // per plane
+    return gp;
+}
+
+static __host__ __device__ __forceinline__ uint64_t tiles_before_band(uint64_t I, uint64_t NB) {
+    // sum_{I' < I} (NB - 2 I') with NB = k-blocks per row = 2 * n_bands
+    return I * NB - I * (I - 1);
+}
+
+size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
+    const uint64_t nb = gp.n_bands;
+    return (size_t)(nb * (nb + 1)) * g::TILE_BYTES;
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation: D -> swizzled BF16 hi/lo tiles of the strict upper triangle
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
+            uint8_t* __restrict__ tiles) {
+    const uint64_t NB = 2ull * n_bands;
+    const uint64_t n_tiles = (uint64_t)n_bands * (n_bands + 1);
+    for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        // band I: largest I with tiles_before_band(I) <= t
+        uint32_t lo = 0, hi = n_bands - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) / 2;
+            if (tiles_before_band(mid, NB) <= t) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t I = lo;
+        const uint32_t kb = (uint32_t)(t - tiles_before_band(I, NB)) + 2 * I;
+        uint8_t* tile = tiles + t * g::TILE_BYTES;
+        const bool diag = kb < 2 * I + 2;
+        for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
+            const uint32_t r = job >> 3, c8 = job & 7;
+            const uint32_t i = I * g::BM + r;
+            const uint32_t j0 = kb * g::BK + c8 * 8;
+            float v[8];
+            if (i < n && vec && !diag && j0 + 7 < n) {
+                const float4* src = reinterpret_cast<const float4*>(mat + (uint64_t)i * ld + j0);
+                const float4 a = __ldg(src), b = __ldg(src + 1);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t j = j0 + e;
+                    v[e] = 0.f;
+                    if (i < n && j < n && j > i) v[e] = __ldg(mat + (uint64_t)i * ld + j);
+                }
+            }
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const uint32_t j = j0 + e;
+                // strict upper triangle only: anything else contributes exactly zero
+                const float d0 = (i < n && j < n && j > i) ? v[e] * v[e] : 0.f;
+                const float d1 = (i < n && j + 1 < n && j + 1 > i) ? v[e + 1] * v[e + 1] : 0.f;
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(d0), h1 = __float2bfloat16_rn(d1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(d0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(d1 - __bfloat162float(h1));
+                hw[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                lw[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const uint32_t off = sw128_offset(r, c8);
+            *reinterpret_cast<uint4*>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(tile + g::PLANE_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+    }
+}
+
+cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s) {
+    const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
+    const uint64_t n_tiles = (uint64_t)gp.n_bands * (gp.n_bands + 1);
+    const unsigned blocks = (unsigned)(n_tiles < 152ull * 16 ? n_tiles : 152ull * 16);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, (uint8_t*)scratch);
+    return launched(1);
+}
+
+// ---------------------------------------------------------------------------
+// the persistent tensor-core kernel
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    const uint8_t* tiles;      // prepared A tiles
+    const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
+    const double* w;
+    double* partials;          // n_bands x P
+    DevStatus* st;
+    uint64_t P;
+    uint64_t n_ptiles;
+    uint32_t n_pad;
+    uint32_t n_bands;
+    uint32_t K;
+    uint32_t ppt;
+    uint32_t N;                // MMA N (multiple of 16, <= 256)
+};
+
+// Bounded wait.  With `obey_abort` the wait also gives up once another role
+// has aborted.  Returns true when the phase completed.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                         DevStatus* st, unsigned where, bool obey_abort = true) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if (obey_abort && *abort_flag) return false;
+        if (clock64() - t0 > g::WAIT_LIMIT) {
+            *abort_flag = 1;
+            raise_status(st, DEV_TIMEOUT, where, 0ull);
+            return false;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + g::OFF_BAR);
+    uint64_t* full = bars;                        // [NST] A tile + labels landed
+    uint64_t* ready = bars + g::NST;              // [NST] B tile built
+    uint64_t* empty = bars + 2 * g::NST;          // [NST] MMAs of the stage done
+    uint64_t* acc_full = bars + 3 * g::NST;       // [2]
+    uint64_t* acc_empty = bars + 3 * g::NST + 2;  // [2]
+    uint64_t* epi_bar = bars + 3 * g::NST + 4;    // epilogue warps meet here once per chunk
+    uint64_t* mma_done = bars + 3 * g::NST + 5;   // final commit of the MMA thread
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
+    uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
+    double* red = reinterpret_cast<double*>(sm + g::OFF_RED);    // [2][4][PPT_MAX]
+    double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);
+    double* wtab = reinterpret_cast<double*>(sm + g::OFF_W);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    DevStatus* st = a.st;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < g::NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(epi_bar, 128);
+        mbar_init(mma_done, 1);
+        *abort_flag = (st->code != DEV_OK) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (uint32_t k = threadIdx.x; k < 256; k += blockDim.x) wtab[k] = k < a.K ? __ldg(a.w + k) : 0.0;
+    // B rows beyond ppt*K stay zero in every stage
+    for (uint32_t e = threadIdx.x; e < g::NST * (g::B_BYTES / 16); e += blockDim.x) {
+        const uint32_t s = e / (g::B_BYTES / 16), o = e % (g::B_BYTES / 16);
+        *reinterpret_cast<uint4*>(sm + s * g::STAGE_BYTES + g::A_BYTES + o * 16) = make_uint4(0, 0, 0, 0);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const uint64_t n_units = (uint64_t)a.n_bands * a.n_ptiles;
+    const uint32_t NB = 2 * a.n_bands;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint64_t kc = 0;
+            int64_t last_round[g::NST] = {-1, -1, -1};
+            bool ok = true;
+            for (uint64_t u = blockIdx.x; u < n_units && ok && !*abort_flag; u += gridDim.x) {
+                const uint32_t I = (uint32_t)(u / a.n_ptiles);
+                const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
+                const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
+                const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
+                for (uint32_t kb = 2 * I; kb < NB; ++kb, ++kc, tile += g::TILE_BYTES) {
+                    const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
+                    if (!wait_bar(&empty[s], (r & 1) ^ 1, abort_flag, st, 1)) { ok = false; break; }
+                    uint8_t* stg = sm + s * g::STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], g::A_BYTES + nlab * g::BK);
+                    bulk_g2s(stg, tile, g::A_BYTES, &full[s]);
+                    const uint8_t* lsrc = a.labels + p0 * a.n_pad + (uint64_t)kb * g::BK;
+                    for (uint32_t p = 0; p < nlab; ++p)
+                        bulk_g2s(stg + g::A_BYTES + g::B_BYTES + p * g::BK, lsrc + (uint64_t)p * a.n_pad,
+                                 g::BK, &full[s]);
+                    last_round[s] = r;
+                }
+            }
+            // every issued copy must land before the CTA exits
+            for (int s = 0; s < g::NST; ++s)
+                if (last_round[s] >= 0)
+                    wait_bar(&full[s], (uint32_t)last_round[s] & 1, abort_flag, st, 7, false);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(g::BM, a.N);
+            uint64_t kc = 0, cc = 0;
+            bool ok = true;
+            for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const uint32_t I = (uint32_t)(u / a.n_ptiles);
+                const uint32_t nkb = NB - 2 * I;
+                for (uint32_t c0 = 0; c0 < nkb && ok; c0 += g::DRAIN_KB, ++cc) {
+                    const uint32_t b = (uint32_t)(cc & 1);
+                    if (!wait_bar(&acc_empty[b], ((uint32_t)(cc >> 1) & 1) ^ 1, abort_flag, st, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + b * g::NMAX;
+                    const uint32_t c1 = min(nkb, c0 + g::DRAIN_KB);
+                    for (uint32_t k = c0; k < c1; ++k, ++kc) {
+                        const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
+                        if (!wait_bar(&full[s], r & 1, abort_flag, st, 3) ||
+                            !wait_bar(&ready[s], r & 1, abort_flag, st, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(sm + s * g::STAGE_BYTES);
+                        const uint32_t sb = sa + g::A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < g::BK / 16; ++kk) {
+                            const uint64_t bd = sw128_desc(sb + kk * 32);
+                            mma_bf16(d_tmem, sw128_desc(sa + kk * 32), bd, idesc, (k > c0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(d_tmem, sw128_desc(sa + g::PLANE_BYTES + kk * 32), bd, idesc, 1u);
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    if (ok) mma_commit(&acc_full[b]);
+                }
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            mma_commit(mma_done);
+            wait_bar(mma_done, 0, abort_flag, st, 8, false);
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t et = threadIdx.x - 128;     // 0..127
+        const uint32_t q4 = warp - 4;              // TMEM lane quarter
+        const uint32_t row = q4 * 32 + lane;       // row within the band
+        const uint32_t K = a.K;
+        uint64_t cc = 0;
+        uint32_t epi_phase = 0;
+        bool ok = true;
+        for (uint32_t p = et; p < g::PPT_MAX; p += 128) acc64[p] = 0.0;
+        for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const uint32_t I = (uint32_t)(u / a.n_ptiles);
+            const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
+            const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
+            // this row's labels for the tile's label rows
+            const uint8_t* lsrc = a.labels + p0 * a.n_pad + (uint64_t)I * g::BM + row;
+            for (uint32_t p = 0; p < a.ppt; ++p)
+                lab_rows[p * g::BM + row] = p < nlab ? __ldg(lsrc + (uint64_t)p * a.n_pad) : (uint8_t)0;
+            const uint32_t nkb = NB - 2 * I;
+            for (uint32_t c0 = 0; c0 < nkb; c0 += g::DRAIN_KB, ++cc) {
+                const uint32_t b = (uint32_t)(cc & 1);
+                if (!wait_bar(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
+                tc_fence_after();
+                double* redc = red + (cc & 1) * 4 * g::PPT_MAX;
+                // walk the accumulator columns c = p*K + gcol; keep column g_p(row) of row p
+                uint32_t p = 0, gcol = 0;
+                uint32_t lab = lab_rows[row];
+                float sel = 0.f;
+                const uint32_t taddr = tmem + ((q4 * 32u) << 16) + b * g::NMAX;
+                for (uint32_t grp = 0; grp < a.N / 32; ++grp) {
+                    uint32_t r[32];
+                    __syncwarp();
+                    tmem_ld32(taddr + grp * 32, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        if (p < a.ppt) {
+                            if (gcol == lab) sel = __uint_as_float(r[k]);
+                            if (++gcol == K) {
+                                double v = (double)sel * wtab[lab];
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                                if (lane == 0) redc[q4 * g::PPT_MAX + p] = v;
+                                ++p;
+                                gcol = 0;
+                                sel = 0.f;
+                                lab = p < a.ppt ? lab_rows[p * g::BM + row] : 0u;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acc_empty[b]);
+                // the four warps' row sums of this chunk, added in a fixed order
+                mbar_arrive(epi_bar);
+                if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 9, false)) { ok = false; break; }
+                ++epi_phase;
+                for (uint32_t pp = et; pp < a.ppt; pp += 128)
+                    acc64[pp] += (redc[pp] + redc[g::PPT_MAX + pp]) +
+                                 (redc[2 * g::PPT_MAX + pp] + redc[3 * g::PPT_MAX + pp]);
+            }
+            if (!ok) break;
+            for (uint32_t pp = et; pp < a.ppt; pp += 128) {
+                if (pp < nlab) a.partials[(uint64_t)I * a.P + p0 + pp] = acc64[pp];
+                acc64[pp] = 0.0;
+            }
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------------------ B builders
+        const uint32_t t = threadIdx.x - 256;      // 0..127
+        const uint32_t K = a.K;
+        const uint32_t rows_used = a.ppt * K;
+        uint64_t kc = 0;
+        bool ok = true;
+        for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const uint32_t I = (uint32_t)(u / a.n_ptiles);
+            const uint32_t nkb = NB - 2 * I;
+            for (uint32_t k = 0; k < nkb; ++k, ++kc) {
+                const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
+                if (!wait_bar(&full[s], r & 1, abort_flag, st, 6)) { ok = false; break; }
+                uint8_t* B = sm + s * g::STAGE_BYTES + g::A_BYTES;
+                const uint8_t* L = B + g::B_BYTES;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t c = t + 128u * h;
+                    if (c < rows_used) {
+                        const uint32_t pl = c / K, gg = c - pl * K;
+                        const uint32_t rep = gg * 0x01010101u;
+#pragma unroll
+                        for (uint32_t c8 = 0; c8 < 8; ++c8) {
+                            const uint2 lw = *reinterpret_cast<const uint2*>(L + pl * g::BK + c8 * 8);
+                            const uint32_t xs[2] = {lw.x ^ rep, lw.y ^ rep};
+                            uint32_t o[4];
+#pragma unroll
+                            for (int hw = 0; hw < 2; ++hw) {
+                                const uint32_t x = xs[hw];
+                                // 0x80 in every byte of x that is zero (label == g), else 0
+                                const uint32_t nz = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+                                const uint32_t eq = ~nz & 0x80808080u;
+                                // spread bytes to 16-bit halves; 0x80 * 0x7F = 0x3F80 = bf16 1.0
+                                o[2 * hw] = __byte_perm(eq, 0u, 0x4140u) * 0x7Fu;
+                                o[2 * hw + 1] = __byte_perm(eq, 0u, 0x4342u) * 0x7Fu;
+                            }
+                            *reinterpret_cast<uint4*>(B + sw128_offset(c, c8)) = make_uint4(o[0], o[1], o[2], o[3]);
+                        }
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(&ready[s]);
+            }
+        }
+    }
+
+    // ---------------------------------------------------------------- teardown
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
+                             double* partials, DevStatus* st, int sm_count, cudaStream_t s) {
+    GemmArgs a;
+    a.tiles = (const uint8_t*)scratch;
+    a.labels = (const uint8_t*)pr.labels;
+    a.w = pr.w;
+    a.partials = partials;
+    a.st = st;
+    a.P = pr.P;
+    a.n_ptiles = gp.n_ptiles;
+    a.n_pad = gp.n_pad;
+    a.n_bands = gp.n_bands;
+    a.K = pr.K;
+    a.ppt = gp.perms_per_tile;
+    a.N = (a.ppt * pr.K + 15) / 16 * 16;
+    if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
+    if (a.ppt == 0 || pr.K > 256 || pr.label_type != LABEL_U8) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)g::SMEM_ALLOC);
+    if (e != cudaSuccess) return e;
+    const uint64_t n_units = (uint64_t)gp.n_bands * gp.n_ptiles;
+    const unsigned grid = (unsigned)(n_units < (uint64_t)sm_count ? n_units : (uint64_t)sm_count);
+    k_gemm_main<<<grid, g::THREADS, g::SMEM_ALLOC, s>>>(a);
+    return launched(1);
+}
+
+}  // namespace pmn

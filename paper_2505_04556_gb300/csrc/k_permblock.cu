@@ -1,0 +1,178 @@
+// Perm-blocked CUDA-core s_W: one 64 x 64 tile of D^2 in shared memory is
+// reused by a block of 128 label rows, one label row per thread.
+//
+// Algorithm 1 evaluates, per label row p and pair i < j, the test
+// g_p(i) == g_p(j) and adds d_ij^2 * w_{g_p(i)} (Sec. 2).  Here a CTA owns a
+// band of 64 rows and 128 label rows and walks the band's column tiles from
+// the diagonal to the end:
+//   * the tile is loaded once (128-bit, coalesced), squared, and masked to the
+//     strict upper triangle (j > i, j < n) before it is stored, so the hot
+//     loop needs no bounds or triangle tests;
+//   * every thread keeps its row's 64 column labels in registers as floats
+//     2^23 + g, so one float compare yields the 0/1 selector, and two
+//     selectors feed one packed FP32x2 FMA (2 evaluations per FFMA2);
+//   * D^2 is read from shared memory with 128-bit broadcast loads;
+//   * as in Algorithm 2, the row segment is summed unweighted and multiplied
+//     by w_{g_p(i)} once.  Row segments (64 terms, four FP32 partial sums)
+//     are weighted and accumulated in FP64; the CTA writes one FP64
+//     partial per (band, label row).
+// Labels arrive as uint8 (K <= 256) or uint16 codes whose row stride is a
+// multiple of 16 bytes, so each thread loads its 64 column labels of a full
+// tile with 16-byte loads (the ragged last tile uses guarded scalar loads).
+#include "common.cuh"
+
+namespace pmn {
+
+constexpr int PB_P = 128;  // label rows per CTA (one per thread)
+constexpr int PB_T = 64;   // band height and column-tile width
+
+__device__ __forceinline__ float code_u8(uint32_t word, int k) {
+    // bytes: [label byte k, 0, 0, 0x4B] -> float 2^23 + label
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7440u | (uint32_t)k));
+}
+__device__ __forceinline__ float code_u16(uint32_t word, int k) {
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, k ? 0x7432u : 0x7410u));
+}
+__device__ __forceinline__ float code_of(uint32_t g) { return __uint_as_float(0x4B000000u | g); }
+
+template <typename L>
+__device__ __forceinline__ void load_col_codes(const L* __restrict__ g, uint32_t j0, float* cl);
+
+template <>
+__device__ __forceinline__ void load_col_codes<uint8_t>(const uint8_t* __restrict__ g, uint32_t j0,
+                                                        float* cl) {
+    const uint4* src = reinterpret_cast<const uint4*>(g + j0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = __ldg(src + q);
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cl[16 * q + 4 * t + k] = code_u8(w4[t], k);
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_col_codes<uint16_t>(const uint16_t* __restrict__ g,
+                                                         uint32_t j0, float* cl) {
+    const uint4* src = reinterpret_cast<const uint4*>(g + j0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint4 v = __ldg(src + q);
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) cl[8 * q + 2 * t + k] = code_u16(w4[t], k);
+    }
+}
+
+template <typename L, bool VEC>
+__global__ void __launch_bounds__(PB_P, 4)
+k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __restrict__ labels,
+               uint64_t lstride, uint64_t P, const double* __restrict__ w, uint32_t K,
+               uint32_t n_pblocks, double* __restrict__ partials, const DevStatus* __restrict__ st) {
+    __shared__ __align__(16) float d2[PB_T][PB_T];
+    const uint32_t band = blockIdx.x / n_pblocks;
+    const uint32_t q = blockIdx.x % n_pblocks;
+    const uint64_t p = (uint64_t)q * PB_P + threadIdx.x;
+    const bool active = p < P;
+    if (st->code != DEV_OK) {
+        if (active) partials[(uint64_t)band * P + p] = 0.0;
+        return;
+    }
+    // inactive threads of the last block mirror the last row so loads stay in bounds
+    const L* g = labels + (active ? p : P - 1) * lstride;
+    const uint32_t r0 = band * PB_T;
+    const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
+    double total = 0.0;
+
+    for (uint32_t j0 = r0; j0 < n; j0 += PB_T) {
+        __syncthreads();  // the previous tile has been consumed
+        // ---- stage the D^2 tile, masked to j > i and j < n ----
+#pragma unroll
+        for (int e = threadIdx.x; e < PB_T * PB_T / 4; e += PB_P) {
+            const int rr = e >> 4, cc = (e & 15) * 4;
+            const uint32_t i = r0 + rr, j = j0 + cc;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) {
+                const float* src = mat + (uint64_t)i * ld + j;
+                if (VEC && j + 3 < n) {
+                    v = __ldg(reinterpret_cast<const float4*>(src));
+                } else {
+                    if (j < n) v.x = __ldg(src);
+                    if (j + 1 < n) v.y = __ldg(src + 1);
+                    if (j + 2 < n) v.z = __ldg(src + 2);
+                    if (j + 3 < n) v.w = __ldg(src + 3);
+                }
+            }
+            v.x = (j > i && j < n) ? v.x * v.x : 0.f;
+            v.y = (j + 1 > i && j + 1 < n) ? v.y * v.y : 0.f;
+            v.z = (j + 2 > i && j + 2 < n) ? v.z * v.z : 0.f;
+            v.w = (j + 3 > i && j + 3 < n) ? v.w * v.w : 0.f;
+            *reinterpret_cast<float4*>(&d2[rr][cc]) = v;
+        }
+        // ---- this thread's 64 column labels (padding beyond n is 0; its D^2 is 0) ----
+        float cl[PB_T];
+        if (j0 + PB_T <= n) {
+            load_col_codes<L>(g, j0, cl);
+        } else {
+#pragma unroll
+            for (int c = 0; c < PB_T; ++c) cl[c] = code_of(j0 + c < n ? (uint32_t)g[j0 + c] : 0u);
+        }
+        __syncthreads();
+
+        for (uint32_t r = 0; r < rows; ++r) {
+            const uint32_t gi = min((uint32_t)g[r0 + r], K - 1);
+            const float fgi = code_of(gi);
+            const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c4 = 0; c4 < PB_T / 4; ++c4) {
+                const float4 dv = drow[c4];
+                const float e0 = (cl[4 * c4 + 0] == fgi) ? 1.f : 0.f;
+                const float e1 = (cl[4 * c4 + 1] == fgi) ? 1.f : 0.f;
+                const float e2 = (cl[4 * c4 + 2] == fgi) ? 1.f : 0.f;
+                const float e3 = (cl[4 * c4 + 3] == fgi) ? 1.f : 0.f;
+                a0 = __ffma2_rn(make_float2(e0, e1), make_float2(dv.x, dv.y), a0);
+                a1 = __ffma2_rn(make_float2(e2, e3), make_float2(dv.z, dv.w), a1);
+            }
+            // weight applied once per row segment (Algorithm 2), accumulated in FP64
+            total = fma((double)((a0.x + a0.y) + (a1.x + a1.y)), __ldg(w + gi), total);
+        }
+    }
+    if (active) partials[(uint64_t)band * P + p] = total;
+}
+
+uint32_t permblock_bands(uint32_t n) { return (n - 1 + PB_T - 1) / PB_T; }
+
+template <typename L>
+static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* partials,
+                               const DevStatus* st, cudaStream_t s) {
+    const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
+    const uint32_t n_bands = permblock_bands(pr.n);
+    const uint64_t n_pblocks = (pr.P + PB_P - 1) / PB_P;
+    const uint64_t blocks = (uint64_t)n_bands * n_pblocks;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    if (vec)
+        k_sw_permblock<L, true><<<(unsigned)blocks, PB_P, 0, s>>>(
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.K,
+            (uint32_t)n_pblocks, partials, st);
+    else
+        k_sw_permblock<L, false><<<(unsigned)blocks, PB_P, 0, s>>>(
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.K,
+            (uint32_t)n_pblocks, partials, st);
+    return launched(1);
+}
+
+// pr.labels must be uint8 (pr.label_type == LABEL_U8) or uint16 codes with a
+// row stride of lstride elements, lstride * sizeof(code) a multiple of 16 and
+// the base address 16-byte aligned.
+cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
+                                      const DevStatus* st, cudaStream_t s) {
+    if (pr.label_type == LABEL_U8) return launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
+    return launch_pb_t<uint16_t>(pr, lstride, partials, st, s);
+}
+
+}  // namespace pmn

@@ -1,0 +1,550 @@
+// Host runtime behind the C ABI of libpermanova (include/permanova.h):
+// argument checks, the kernel-form planner, the context's scratch arena, and
+// the orchestration of the s_W path and the permutation test.
+#include "../../include/permanova.h"
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace pmn;
+
+struct permanova_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    int forced_form = PERMANOVA_FORM_AUTO;
+    std::mutex mu;
+    void* arena = nullptr;
+    size_t arena_size = 0;
+    DevStatus* status = nullptr;        // device error word
+    DevStatus* status_host = nullptr;   // pinned mirror
+    TestScalars* scalars = nullptr;     // device
+    TestScalars* scalars_host = nullptr;
+    // profiling
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    uint64_t launch_mark = 0;
+    int last_form = 0;
+};
+
+namespace {
+
+thread_local std::string tl_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    tl_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+    return fail(e == cudaErrorMemoryAllocation ? PERMANOVA_ENOMEM : PERMANOVA_ECUDA, "%s: %s (%s)",
+                what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// Scratch carve-up for one s_W call.
+struct SWLayout {
+    int form = 0;
+    uint32_t part_rows = 0;     // rows of the FP64 partials table
+    size_t part_off = 0;
+    bool repack = false;        // labels re-laid out as codes
+    int code_type = LABEL_U8;
+    uint64_t lstride = 0;
+    size_t lab_off = 0;
+    size_t gemm_off = 0;
+    size_t w_off = 0;           // n_groups FP64 weights
+    size_t total = 0;
+};
+
+int label_bytes(int t) { return t == LABEL_U8 ? 1 : t == LABEL_U16 ? 2 : 4; }
+
+int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
+    if (ctx->forced_form != PERMANOVA_FORM_AUTO) return ctx->forced_form;
+    // The tensor-core form costs 4K flops per pair and label row (two BF16
+    // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
+    // At the measured rates the GEMM form wins up to about K = 20.
+    if (gemm_available() && K <= 20 && n >= 256 && P >= 32) return PERMANOVA_FORM_GEMM;
+    if (P >= 16 && K <= 65536) return PERMANOVA_FORM_PERMBLOCK;
+    return PERMANOVA_FORM_BRUTE;
+}
+
+int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, const void* labels,
+               int label_type, uint32_t K, uint64_t P, SWLayout* L) {
+    *L = SWLayout{};
+    L->form = form;
+    size_t off = 0;
+    if (form == PERMANOVA_FORM_BRUTE) {
+        L->part_rows = brute_chunks(n, ctx->sm_count);
+    } else if (form == PERMANOVA_FORM_PERMBLOCK) {
+        if (K > 65536)
+            return fail(PERMANOVA_EUNSUPPORTED, "perm-block form needs n_groups <= 65536 (got %u)", K);
+        L->part_rows = permblock_bands(n);
+        L->code_type = K <= 256 ? LABEL_U8 : LABEL_U16;
+        const bool direct = labels != nullptr && (label_type == L->code_type) &&
+                            ((uint64_t)n * label_bytes(label_type)) % 16 == 0 &&
+                            ((uintptr_t)labels % 16 == 0);
+        L->repack = !direct;
+        L->lstride = direct ? n : (uint64_t)align_up(n, 64);
+    } else if (form == PERMANOVA_FORM_GEMM) {
+        if (!gemm_available()) return fail(PERMANOVA_EUNSUPPORTED, "GEMM form not built");
+        if (K > 256) return fail(PERMANOVA_EUNSUPPORTED, "GEMM form needs n_groups <= 256 (got %u)", K);
+        if (n < 2) return fail(PERMANOVA_EINVAL, "n_dims < 2");
+        const GemmPlan gp = gemm_plan(n, K, P);
+        L->part_rows = gp.n_bands;
+        L->code_type = LABEL_U8;
+        L->repack = true;  // the GEMM form reads 16-byte aligned, zero-padded uint8 rows
+        L->lstride = gp.n_pad;
+    } else {
+        return fail(PERMANOVA_EINVAL, "unknown form %d", form);
+    }
+    (void)ld;
+    L->part_off = off;
+    off = align_up(off + (size_t)L->part_rows * P * sizeof(double));
+    if (L->repack) {
+        L->lab_off = off;
+        off = align_up(off + (size_t)L->lstride * P * label_bytes(L->code_type));
+    }
+    if (form == PERMANOVA_FORM_GEMM) {
+        const GemmPlan gp = gemm_plan(n, K, P);
+        L->gemm_off = off;
+        off = align_up(off + gemm_scratch_bytes(gp, P));
+    }
+    L->w_off = off;
+    off = align_up(off + (size_t)K * sizeof(double));
+    L->total = off;
+    return PERMANOVA_OK;
+}
+
+// Make the arena at least `bytes`.  Growing waits for all device work (the
+// old arena may still be in use) before it is replaced.
+int ensure_arena(permanova_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->arena_size) return PERMANOVA_OK;
+    if (bytes > ctx->budget)
+        return fail(PERMANOVA_ENOMEM, "scratch of %zu bytes exceeds the context budget of %zu bytes",
+                    bytes, ctx->budget);
+    size_t want = std::min(ctx->budget, std::max(bytes, ctx->arena_size + ctx->arena_size / 4));
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (ctx->arena) {
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_size = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess && want > bytes) {
+        cudaGetLastError();
+        want = bytes;
+        e = cudaMalloc(&p, want);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
+    ctx->arena = p;
+    ctx->arena_size = want;
+    return PERMANOVA_OK;
+}
+
+int check_sW_args(const float* mat, uint32_t n, uint64_t ld, const void* labels, int label_type,
+                  uint32_t K, uint64_t P, const float* w, const double* out) {
+    if (!mat || !labels || !w || !out) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (n < 2) return fail(PERMANOVA_EINVAL, "n_dims must be >= 2 (got %u)", n);
+    if (ld < n) return fail(PERMANOVA_EINVAL, "ld (%llu) < n_dims (%u)", (unsigned long long)ld, n);
+    if (K == 0) return fail(PERMANOVA_EINVAL, "n_groups must be >= 1");
+    if (P == 0) return fail(PERMANOVA_EINVAL, "n_perms must be >= 1");
+    if (label_type != LABEL_I32 && label_type != LABEL_U16 && label_type != LABEL_U8)
+        return fail(PERMANOVA_EINVAL, "unknown label type %d", label_type);
+    if (label_type == LABEL_U8 && K > 256)
+        return fail(PERMANOVA_EINVAL, "uint8 labels hold at most 256 groups (n_groups = %u)", K);
+    if (label_type == LABEL_U16 && K > 65536)
+        return fail(PERMANOVA_EINVAL, "uint16 labels hold at most 65536 groups (n_groups = %u)", K);
+    return PERMANOVA_OK;
+}
+
+// Events around the dominant kernel of an s_W call (profiling only).
+int profile_begin(permanova_ctx* ctx, cudaStream_t s) {
+    if (!ctx->profiling) return PERMANOVA_OK;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a), "cudaEventCreate");
+    CK(cudaEventCreate(&b), "cudaEventCreate");
+    ctx->events.emplace_back(a, b);
+    CK(cudaEventRecord(a, s), "cudaEventRecord");
+    return PERMANOVA_OK;
+}
+
+int profile_end(permanova_ctx* ctx, cudaStream_t s) {
+    if (!ctx->profiling || ctx->events.empty()) return PERMANOVA_OK;
+    CK(cudaEventRecord(ctx->events.back().second, s), "cudaEventRecord");
+    return PERMANOVA_OK;
+}
+
+void profile_clear(permanova_ctx* ctx) {
+    for (auto& e : ctx->events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    ctx->events.clear();
+    ctx->launch_mark = kernel_launch_count();
+}
+
+// The s_W path on device buffers; the arena is already large enough.
+// `wf` (device fp32 inv_group_sizes) is widened into the layout's FP64 slot;
+// with wf == NULL the slot already holds the weights.
+int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s) {
+    char* base = static_cast<char*>(ctx->arena);
+    double* partials = reinterpret_cast<double*>(base + L.part_off);
+    double* wd = reinterpret_cast<double*>(base + L.w_off);
+    if (wf) CK(launch_widen(wf, pr.K, wd, s), "widen weights");
+    pr.w = wd;
+    SWProblem q = pr;
+    if (L.form == PERMANOVA_FORM_BRUTE) {
+        CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K, ctx->status, s),
+           "validate labels");
+        int rc = profile_begin(ctx, s);
+        if (rc) return rc;
+        CK(launch_brute(pr, L.part_rows, partials, ctx->status, s), "brute-force kernel");
+        rc = profile_end(ctx, s);
+        if (rc) return rc;
+    } else {
+        if (L.repack) {
+            void* codes = base + L.lab_off;
+            CK(launch_repack_labels(pr.labels, pr.label_type, pr.n, pr.P, pr.K, codes, L.code_type,
+                                    L.lstride, ctx->status, s),
+               "repack labels");
+            q.labels = codes;
+            q.label_type = L.code_type;
+        } else {
+            CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K,
+                                      ctx->status, s),
+               "validate labels");
+        }
+        if (L.form == PERMANOVA_FORM_PERMBLOCK) {
+            int rc = profile_begin(ctx, s);
+            if (rc) return rc;
+            CK(launch_permblock_internal(q, L.lstride, partials, ctx->status, s), "perm-block kernel");
+            rc = profile_end(ctx, s);
+            if (rc) return rc;
+        } else {
+            const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P);
+            void* gs = base + L.gemm_off;
+            CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
+            int rc = profile_begin(ctx, s);
+            if (rc) return rc;
+            CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s), "GEMM kernel");
+            rc = profile_end(ctx, s);
+            if (rc) return rc;
+        }
+    }
+    CK(launch_reduce_rows(partials, L.part_rows, pr.P, pr.out, s), "reduce partials");
+    ctx->last_form = L.form;
+    return PERMANOVA_OK;
+}
+
+int read_status(permanova_ctx* ctx, cudaStream_t s) {
+    CK(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s),
+       "read device status");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    DevStatus h = *ctx->status_host;
+    if (h.code == DEV_OK) return PERMANOVA_OK;
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s), "reset device status");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (h.code == DEV_BAD_LABEL)
+        return fail(PERMANOVA_EINVAL, "label >= n_groups at flat index %llu", h.info);
+    if (h.code == DEV_TIMEOUT)
+        return fail(PERMANOVA_ETIMEOUT, "device wait timed out (kernel stage %u, detail %llu)", h.where,
+                    h.info);
+    return fail(PERMANOVA_ECUDA, "device error code %u", h.code);
+}
+
+}  // namespace
+
+extern "C" {
+
+int permanova_create(int device, size_t hbm_budget_bytes, permanova_ctx** out) {
+    if (!out) return fail(PERMANOVA_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    CK(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+    if (device < 0 || device >= count)
+        return fail(PERMANOVA_EINVAL, "device %d out of range (%d devices)", device, count);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(PERMANOVA_ECUDA, "cannot select device %d", device);
+    auto* ctx = new permanova_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 10 * 9;
+    cudaError_t e = cudaMalloc(&ctx->status, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->status_host, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->scalars, sizeof(TestScalars));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->scalars_host, sizeof(TestScalars));
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "context allocation");
+        permanova_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return PERMANOVA_OK;
+}
+
+void permanova_destroy(permanova_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        profile_clear(ctx);
+        if (ctx->arena) cudaFree(ctx->arena);
+        if (ctx->status) cudaFree(ctx->status);
+        if (ctx->status_host) cudaFreeHost(ctx->status_host);
+        if (ctx->scalars) cudaFree(ctx->scalars);
+        if (ctx->scalars_host) cudaFreeHost(ctx->scalars_host);
+    }
+    delete ctx;
+}
+
+const char* permanova_last_error(const permanova_ctx*) { return tl_err.c_str(); }
+
+int permanova_set_form(permanova_ctx* ctx, int form) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    if (form < PERMANOVA_FORM_AUTO || form > PERMANOVA_FORM_GEMM)
+        return fail(PERMANOVA_EINVAL, "unknown form %d", form);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->forced_form = form;
+    return PERMANOVA_OK;
+}
+
+int permanova_plan_form(permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return plan_form(ctx, n, K, P);
+}
+
+size_t permanova_scratch_bytes(permanova_ctx* ctx, int form, uint32_t n, uint32_t K, uint64_t P) {
+    if (!ctx || n < 2 || K == 0 || P == 0) return 0;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (form == PERMANOVA_FORM_AUTO) form = plan_form(ctx, n, K, P);
+    SWLayout L;
+    // worst case: labels need a repack
+    if (layout_for(ctx, form, n, n, nullptr, LABEL_I32, K, P, &L) != PERMANOVA_OK) return 0;
+    return L.total;
+}
+
+int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, const void* groupings,
+                 int label_type, uint32_t K, uint64_t P, const float* w, double* out, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    int rc = check_sW_args(mat, n, ld, groupings, label_type, K, P, w, out);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SWLayout L;
+    rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, groupings, label_type, K, P, &L);
+    if (rc) return rc;
+    rc = ensure_arena(ctx, L.total);
+    if (rc) return rc;
+    SWProblem pr{mat, n, ld, groupings, label_type, K, P, nullptr, out};
+    return run_sW(ctx, L, pr, w, s);
+}
+
+int permanova_profile_enable(permanova_ctx* ctx, int enable) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    profile_clear(ctx);
+    ctx->profiling = enable != 0;
+    return PERMANOVA_OK;
+}
+
+int permanova_profile_read(permanova_ctx* ctx, permanova_profile_t* out) {
+    if (!ctx || !out) return fail(PERMANOVA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    double ms = 0.0;
+    for (auto& e : ctx->events) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e.first, e.second), "cudaEventElapsedTime");
+        ms += t;
+    }
+    out->main_kernel_ms = ms;
+    out->main_kernel_launches = ctx->events.size();
+    out->kernel_launches = kernel_launch_count() - ctx->launch_mark;
+    out->last_form = ctx->last_form;
+    profile_clear(ctx);
+    return PERMANOVA_OK;
+}
+
+int permanova_sync(permanova_ctx* ctx, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    return read_status(ctx, static_cast<cudaStream_t>(stream));
+}
+
+int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                      const void* groupings, int label_type, uint32_t K, uint64_t P, const float* w,
+                      double* out, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    int rc = check_sW_args(mat, n, ld, groupings, label_type, K, P, w, out);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SWLayout L;
+    rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
+    if (rc) return rc;
+    // staging for the inputs and the output after the s_W scratch
+    const size_t mat_bytes = (size_t)n * ld * sizeof(float);
+    const size_t lab_bytes = (size_t)n * P * label_bytes(label_type);
+    size_t off = L.total;
+    const size_t mat_off = off;
+    off = align_up(off + mat_bytes);
+    const size_t lab_off = off;
+    off = align_up(off + lab_bytes);
+    const size_t w_off = off;
+    off = align_up(off + (size_t)K * sizeof(float));
+    const size_t out_off = off;
+    off = align_up(off + (size_t)P * sizeof(double));
+    rc = ensure_arena(ctx, off);
+    if (rc) return rc;
+    char* base = static_cast<char*>(ctx->arena);
+    CK(cudaMemcpyAsync(base + mat_off, mat, mat_bytes, cudaMemcpyHostToDevice, s), "copy mat");
+    CK(cudaMemcpyAsync(base + lab_off, groupings, lab_bytes, cudaMemcpyHostToDevice, s), "copy labels");
+    CK(cudaMemcpyAsync(base + w_off, w, (size_t)K * sizeof(float), cudaMemcpyHostToDevice, s),
+       "copy weights");
+    // the staged label buffer is 256-byte aligned: re-plan so the direct path can be taken
+    rc = layout_for(ctx, L.form, n, ld, base + lab_off, label_type, K, P, &L);
+    if (rc) return rc;
+    SWProblem pr{reinterpret_cast<const float*>(base + mat_off), n, ld, base + lab_off, label_type, K,
+                 P, nullptr, reinterpret_cast<double*>(base + out_off)};
+    rc = run_sW(ctx, L, pr, reinterpret_cast<const float*>(base + w_off), s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, base + out_off, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "copy results");
+    return read_status(ctx, s);
+}
+
+int permanova_permutations(permanova_ctx* ctx, const int32_t* grouping, uint32_t n, uint32_t K,
+                           uint64_t n_perms, uint64_t seed, void* out, int label_type, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    if (!grouping || !out) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (n < 2) return fail(PERMANOVA_EINVAL, "n_dims must be >= 2");
+    if (n_perms == 0 || n_perms >= 0xFFFFFFFFull) return fail(PERMANOVA_EINVAL, "n_perms out of range");
+    if (label_type != LABEL_I32 && label_type != LABEL_U16 && label_type != LABEL_U8)
+        return fail(PERMANOVA_EINVAL, "unknown label type %d", label_type);
+    if ((label_type == LABEL_U8 && K > 256) || (label_type == LABEL_U16 && K > 65536))
+        return fail(PERMANOVA_EINVAL, "label type too narrow for %u groups", K);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(launch_permutations(grouping, n, n_perms, seed, out, label_type, static_cast<cudaStream_t>(stream)),
+       "permutation kernels");
+    return PERMANOVA_OK;
+}
+
+int permanova_test(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                   const int32_t* grouping, uint32_t K, uint64_t P, uint64_t seed,
+                   permanova_result* out_host, double* out_sW, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    if (!mat || !grouping || !out_host) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (K < 2) return fail(PERMANOVA_EINVAL, "the test needs n_groups >= 2 (got %u)", K);
+    if (n <= K) return fail(PERMANOVA_EINVAL, "the test needs n_dims > n_groups (pseudo-F undefined)");
+    if (ld < n) return fail(PERMANOVA_EINVAL, "ld < n_dims");
+    if (P == 0 || P >= 0xFFFFFFFFull) return fail(PERMANOVA_EINVAL, "n_perms out of range");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // group sizes -> inv_group_sizes (host), observed labels checked here
+    std::vector<int32_t> hg(n);
+    CK(cudaMemcpyAsync(hg.data(), grouping, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+       "copy grouping");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    std::vector<uint64_t> sizes(K, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (hg[i] < 0 || (uint32_t)hg[i] >= K)
+            return fail(PERMANOVA_EINVAL, "grouping[%u] = %d outside [0, %u)", i, hg[i], K);
+        sizes[hg[i]] += 1;
+    }
+    std::vector<double> hw(K);   // inv_group_sizes 1/n_g, kept in FP64
+    for (uint32_t k = 0; k < K; ++k) {
+        if (sizes[k] == 0) return fail(PERMANOVA_EINVAL, "group %u is empty", k);
+        hw[k] = 1.0 / (double)sizes[k];
+    }
+
+    const uint64_t rows = P + 1;
+    const int lt = K <= 256 ? LABEL_U8 : K <= 65536 ? LABEL_U16 : LABEL_I32;
+    SWLayout L;
+    int rc = layout_for(ctx, plan_form(ctx, n, K, rows), n, ld, nullptr, lt, K, rows, &L);
+    if (rc) return rc;
+    size_t off = L.total;
+    const size_t lab_off = off;
+    off = align_up(off + (size_t)n * rows * label_bytes(lt));
+    const size_t sw_off = off;
+    off = align_up(off + (size_t)rows * sizeof(double));
+    const uint32_t chunks = brute_chunks(n, ctx->sm_count);
+    const size_t st_off = off;
+    off = align_up(off + (size_t)(chunks + 1) * sizeof(double));
+    rc = ensure_arena(ctx, off);
+    if (rc) return rc;
+    char* base = static_cast<char*>(ctx->arena);
+    void* labels = base + lab_off;
+    double* sW = out_sW ? out_sW : reinterpret_cast<double*>(base + sw_off);
+    double* st_part = reinterpret_cast<double*>(base + st_off);
+
+    CK(launch_permutations(grouping, n, P, seed, labels, lt, s), "permutation kernels");
+    rc = layout_for(ctx, L.form, n, ld, labels, lt, K, rows, &L);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(base + L.w_off, hw.data(), (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s),
+       "copy weights");
+    SWProblem pr{mat, n, ld, labels, lt, K, rows, nullptr, sW};
+    rc = run_sW(ctx, L, pr, nullptr, s);
+    if (rc) return rc;
+    CK(launch_sumsq_triangle(mat, n, ld, chunks, st_part, s), "sum of squares kernel");
+    CK(launch_reduce_rows(st_part, chunks, 1, st_part + chunks, s), "reduce s_T");
+    CK(launch_finalize(sW, P, st_part + chunks, n, K, ctx->scalars, s), "finalize kernel");
+    CK(cudaMemcpyAsync(ctx->scalars_host, ctx->scalars, sizeof(TestScalars), cudaMemcpyDeviceToHost, s),
+       "copy result");
+    rc = read_status(ctx, s);
+    if (rc) return rc;
+    const TestScalars& t = *ctx->scalars_host;
+    out_host->s_T = t.s_T;
+    out_host->s_W_obs = t.s_W_obs;
+    out_host->F_obs = t.F_obs;
+    out_host->p_value = t.p_value;
+    out_host->n_ge = t.n_ge;
+    out_host->n_perms = t.n_perms;
+    return PERMANOVA_OK;
+}
+
+}  // extern "C"

@@ -73,11 +73,14 @@ def gaussian_points(labels, dim: int, shift: float, seed: int) -> np.ndarray:
 def euclidean_matrix(X) -> np.ndarray:
     """Dense fp32 Euclidean distance matrix (zero diagonal), computed in float64."""
     X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
     sq = np.einsum("ij,ij->i", X, X)
-    G = X @ X.T
-    D2 = sq[:, None] + sq[None, :] - 2.0 * G
-    np.maximum(D2, 0.0, out=D2)
-    D = np.sqrt(D2).astype(np.float32)
+    D = np.empty((n, n), dtype=np.float32)
+    for r0 in range(0, n, 2048):
+        r1 = min(n, r0 + 2048)
+        D2 = sq[r0:r1, None] + sq[None, :] - 2.0 * (X[r0:r1] @ X.T)
+        np.maximum(D2, 0.0, out=D2)
+        D[r0:r1] = np.sqrt(D2)
     np.fill_diagonal(D, 0.0)
     return D
 

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span several 64/128-wide tiles and ragged tails; label types, group
+counts, label-row counts and strides cover the cases the kernels branch on.
+Tolerance: the stated 1e-5 relative for s_W and pseudo-F; integer-valued
+matrices with power-of-two group sizes must match bit for bit; label
+generation, exceedance counts and p-values are compared exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2505_04556_gb300 as pm  # noqa: E402
+
+RTOL = 1e-5
+FORMS = [pytest.param(pm.FORM_BRUTE, id="brute"), pytest.param(pm.FORM_PERMBLOCK, id="permblock"),
+         pytest.param(pm.FORM_GEMM, id="gemm")]
+FORM_VALUES = [pm.FORM_BRUTE, pm.FORM_PERMBLOCK, pm.FORM_GEMM]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pm.build()
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _label_tensor(rows, ltype):
+    dt = {pm.LABEL_U8: torch.uint8, pm.LABEL_U16: torch.int16, pm.LABEL_I32: torch.int32}[ltype]
+    npdt = {pm.LABEL_U8: np.uint8, pm.LABEL_U16: np.uint16, pm.LABEL_I32: np.int32}[ltype]
+    a = np.ascontiguousarray(rows.astype(npdt))
+    if ltype == pm.LABEL_U16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).cuda(), dt
+
+
+def _run_sW(ctx, D, rows, K, w, form, ltype=pm.LABEL_I32, ld=None):
+    n = D.shape[0]
+    ld = ld or n
+    Dp = np.zeros((n, ld), dtype=np.float32)
+    Dp[:, :n] = D
+    Dd = _dev(Dp)
+    lab, _ = _label_tensor(rows, ltype)
+    wd = _dev(np.asarray(w, dtype=np.float32))
+    out = torch.empty(rows.shape[0], dtype=torch.float64, device="cuda")
+    ctx.set_form(form)
+    try:
+        pm.permanova_sW(ctx.handle, Dd, n, ld, lab, ltype, K, rows.shape[0], wd, out)
+        pm.permanova_sync(ctx.handle)
+    finally:
+        ctx.set_form(pm.FORM_AUTO)
+    return out.cpu().numpy()
+
+
+def _case(n, K, P, seed, kind="euclid"):
+    rng = np.random.default_rng(seed)
+    if kind == "euclid":
+        X = rng.standard_normal((n, 8))
+        D = synth.euclidean_matrix(X)
+    else:
+        C = synth.dirichlet_compositions(rng.integers(0, K, n), features=40, seed=seed)
+        D = synth.braycurtis_matrix(C)
+    sizes = synth.largest_remainder_sizes(n, rng.dirichlet(2 * np.ones(K)), min_size=1)
+    obs = synth.observed_labels(sizes, seed + 1)
+    rows = synth.shuffled_rows(obs, P, seed + 2)
+    return D, rows, synth.inv_sizes(obs, K)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n,K,P", [(2, 1, 1), (63, 2, 3), (130, 3, 129), (257, 5, 40),
+                                   (300, 10, 131), (1001, 4, 17)])
+def test_sW_matches_oracle(ctx, form, n, K, P):
+    D, rows, w = _case(n, K, P, seed=n * 7 + K)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    got = _run_sW(ctx, D, rows, K, w, form, pm.LABEL_U8)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-12)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ltype", [pm.LABEL_I32, pm.LABEL_U16, pm.LABEL_U8])
+def test_label_types_and_padded_stride(ctx, form, ltype):
+    D, rows, w = _case(200, 6, 70, seed=ltype + 11, kind="braycurtis")
+    ref = oracle.sW_alg1(D, rows, 6, w.astype(np.float64))
+    got = _run_sW(ctx, D, rows, 6, w, form, ltype, ld=203)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-12)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("K,ltype", [(255, pm.LABEL_U8), (256, pm.LABEL_U8), (300, pm.LABEL_U16)])
+def test_many_groups(ctx, form, K, ltype):
+    if form == pm.FORM_GEMM and K > 256:
+        pytest.skip("GEMM form holds at most 256 groups")
+    rng = np.random.default_rng(K)
+    n = 700
+    D = synth.euclidean_matrix(rng.standard_normal((n, 4)))
+    rows = rng.integers(0, K, size=(9, n)).astype(np.int32)
+    w = rng.uniform(0.01, 1.0, K).astype(np.float32)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    got = _run_sW(ctx, D, rows, K, w, form, ltype)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-12)
+
+
+@pytest.mark.parametrize("form", FORMS[:2])
+def test_integer_matrix_bit_exact(ctx, form):
+    # entries in 0..15, groups 64/32/32: every partial sum is exact in FP32/FP64
+    n = 128
+    D = synth.integer_matrix(n, 15, 5)
+    obs = synth.observed_labels([64, 32, 32], 6)
+    rows = synth.shuffled_rows(obs, 33, 7)
+    w = synth.inv_sizes(obs, 3)
+    ref = oracle.sW_alg1(D, rows, 3, w.astype(np.float64))
+    got = _run_sW(ctx, D, rows, 3, w, form)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_lower_triangle_never_read(ctx, form):
+    D, rows, w = _case(190, 3, 20, seed=3)
+    clean = _run_sW(ctx, D, rows, 3, w, form)
+    dirty = _run_sW(ctx, synth.poison_lower(D), rows, 3, w, form)
+    assert np.all(np.isfinite(dirty))
+    assert np.array_equal(clean, dirty)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_deterministic(ctx, form):
+    D, rows, w = _case(333, 4, 300, seed=9)
+    a = _run_sW(ctx, D, rows, 4, w, form)
+    b = _run_sW(ctx, D, rows, 4, w, form)
+    assert np.array_equal(a, b)
+
+
+def test_forms_agree(ctx):
+    D, rows, w = _case(500, 4, 200, seed=21)
+    res = [_run_sW(ctx, D, rows, 4, w, f) for f in FORM_VALUES]
+    for r in res[1:]:
+        np.testing.assert_allclose(r, res[0], rtol=RTOL)
+
+
+def test_single_group_closed_form(ctx):
+    n = 517
+    X = np.random.default_rng(4).standard_normal((n, 6))
+    D = synth.euclidean_matrix(X)
+    rows = np.zeros((3, n), dtype=np.int32)
+    for form in FORM_VALUES:
+        got = _run_sW(ctx, D, rows, 1, [1.0 / n], form)
+        st = oracle.sT(D)
+        np.testing.assert_allclose(got, st, rtol=RTOL)
+
+
+def test_permutations_bit_exact_with_oracle(ctx):
+    obs = synth.observed_labels([37, 20, 13, 3], 12)
+    n = obs.size
+    for ltype, tdt in ((pm.LABEL_I32, torch.int32), (pm.LABEL_U8, torch.uint8),
+                       (pm.LABEL_U16, torch.int16)):
+        out = torch.empty((51, n), dtype=tdt, device="cuda")
+        pm.permanova_permutations(ctx.handle, _dev(obs), n, 4, 50, 9013, out, ltype)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.int64) & (0xFFFF if ltype == pm.LABEL_U16 else -1)
+        ref = oracle.permutations(obs, 50, 9013)
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("n,K,P,seed", [(60, 2, 99, 1), (257, 3, 999, 2), (1000, 3, 999, 3)])
+def test_permanova_test_matches_oracle(ctx, n, K, P, seed):
+    cfg = synth.recipe("euclid-1k", n=n, P=P)
+    X = synth.recipe_points(cfg)
+    D = synth.euclidean_matrix(X)
+    obs = cfg["labels"] if K == 3 else synth.observed_labels([n // 2, n - n // 2], seed)
+    ref = oracle.permanova_test(D, obs, K, P, seed)
+    out_sW = torch.empty(P + 1, dtype=torch.float64, device="cuda")
+    res = pm.permanova_test(ctx.handle, _dev(D), n, n, _dev(obs), K, P, seed, out_sW)
+    sW = out_sW.cpu().numpy()
+    np.testing.assert_allclose(sW, ref["s_W"], rtol=RTOL)
+    assert abs(res["s_T"] - ref["s_T"]) <= RTOL * ref["s_T"]
+    assert abs(res["F_obs"] - ref["F"][0]) <= RTOL * abs(ref["F"][0])
+    # exceedance counts are exact outside the ambiguity band |s_W - s_W_obs| <= 1e-5 s_W_obs
+    band = np.abs(ref["s_W"][1:] - ref["s_W"][0]) <= RTOL * ref["s_W"][0]
+    if not band.any():
+        assert res["n_ge"] == ref["n_ge"]
+        assert res["p_value"] == ref["p_value"]
+    assert res["n_perms"] == P
+
+
+def test_invalid_label_reported(ctx):
+    D, rows, w = _case(100, 3, 5, seed=1)
+    rows = rows.copy()
+    rows[2, 17] = 3
+    for form in FORM_VALUES:
+        with pytest.raises(pm.PermanovaError) as ei:
+            _run_sW(ctx, D, rows, 3, w, form)
+        assert ei.value.status == pm.EINVAL
+    # the context stays usable
+    ok = _run_sW(ctx, D, rows % 3, 3, w, pm.FORM_BRUTE)
+    assert np.all(np.isfinite(ok))
+
+
+def test_argument_errors(ctx):
+    Dd = torch.zeros((10, 10), device="cuda")
+    lab = torch.zeros((1, 10), dtype=torch.uint8, device="cuda")
+    w = torch.ones(2, device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    h = ctx.handle
+    cases = [
+        dict(n=1, ld=10, K=2, P=1, lt=pm.LABEL_U8),
+        dict(n=10, ld=9, K=2, P=1, lt=pm.LABEL_U8),
+        dict(n=10, ld=10, K=0, P=1, lt=pm.LABEL_U8),
+        dict(n=10, ld=10, K=2, P=0, lt=pm.LABEL_U8),
+        dict(n=10, ld=10, K=257, P=1, lt=pm.LABEL_U8),
+        dict(n=10, ld=10, K=2, P=1, lt=7),
+    ]
+    for c in cases:
+        with pytest.raises(pm.PermanovaError) as ei:
+            pm.permanova_sW(h, Dd, c["n"], c["ld"], lab, c["lt"], c["K"], c["P"], w, out)
+        assert ei.value.status == pm.EINVAL
+    with pytest.raises(pm.PermanovaError) as ei:
+        pm.permanova_sW(h, None, 10, 10, lab, pm.LABEL_U8, 2, 1, w, out)
+    assert ei.value.status == pm.EINVAL
+    g = torch.zeros(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(pm.PermanovaError) as ei:   # K < 2
+        pm.permanova_test(h, Dd, 10, 10, g, 1, 10, 1)
+    assert ei.value.status == pm.EINVAL
+    with pytest.raises(pm.PermanovaError) as ei:   # empty group 1
+        pm.permanova_test(h, Dd, 10, 10, g, 2, 10, 1)
+    assert ei.value.status == pm.EINVAL
+
+
+def test_budget_enforced():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    small = pm.Context(0, hbm_budget_bytes=4096)
+    try:
+        D, rows, w = _case(400, 3, 300, seed=2)
+        with pytest.raises(pm.PermanovaError) as ei:
+            _run_sW(small, D, rows, 3, w, pm.FORM_PERMBLOCK)
+        assert ei.value.status == pm.ENOMEM
+    finally:
+        small.close()
+
+
+def test_gemm_rejects_too_many_groups(ctx):
+    D, rows, w = _case(100, 3, 5, seed=1)
+    with pytest.raises(pm.PermanovaError) as ei:
+        _run_sW(ctx, D, rows, 300, np.ones(300, np.float32), pm.FORM_GEMM, pm.LABEL_U16)
+    assert ei.value.status == pm.EUNSUPPORTED
+
+
+def test_host_entry_point(ctx):
+    D, rows, w = _case(321, 4, 50, seed=31)
+    ref = oracle.sW_alg1(D, rows, 4, w.astype(np.float64))
+    out = np.zeros(50, dtype=np.float64)
+    lab = np.ascontiguousarray(rows.astype(np.uint8))
+    pm.permanova_sW_host(ctx.handle, np.ascontiguousarray(D), 321, 321, lab, pm.LABEL_U8, 4, 50,
+                         np.ascontiguousarray(w), out)
+    np.testing.assert_allclose(out, ref, rtol=RTOL)

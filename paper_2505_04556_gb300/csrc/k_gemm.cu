@@ -13,7 +13,7 @@
 // hi + lo carries 16 significant bits (relative error <= 2^-17 per term); the
 // one-hot operand is exact in BF16.  Both planes multiply the same B operand
 // into one FP32 accumulator in tensor memory.  The accumulator is drained
-// every DRAIN_KB k-blocks (1,024 columns); the drained row values are
+// every drain_kb k-blocks (default 16 = 1,024 columns); the drained row values are
 // weighted in FP64, reduced over the 128 rows in a fixed order and
 // accumulated in FP64.
 //
@@ -40,6 +40,8 @@
 
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+
 namespace pmn {
 
 namespace g {
@@ -48,7 +50,7 @@ constexpr int BK = 64;              // k-block width (one 128-byte swizzle atom 
 constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
 constexpr int PPT_MAX = 64;         // label rows per tile
 constexpr int NST = 3;              // pipeline stages
-constexpr int DRAIN_KB = 16;        // k-blocks per accumulator chunk
+constexpr int DRAIN_KB = 16;        // default k-blocks per accumulator chunk
 constexpr int THREADS = 384;
 constexpr uint32_t PLANE_BYTES = BM * BK * 2;             // 16 KB
 constexpr uint32_t TILE_BYTES = 2 * PLANE_BYTES;          // hi + lo planes: 32 KB
@@ -285,6 +287,7 @@ struct GemmArgs {
     uint32_t K;
     uint32_t ppt;
     uint32_t N;                // MMA N (multiple of 16, <= 256)
+    uint32_t drain_kb;         // k-blocks accumulated in TMEM between drains
 };
 
 // Bounded wait.  With `obey_abort` the wait also gives up once another role
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const uint32_t I = (uint32_t)(u / a.n_ptiles);
                 const uint32_t nkb = NB - 2 * I;
-                for (uint32_t c0 = 0; c0 < nkb && ok; c0 += g::DRAIN_KB, ++cc) {
+                for (uint32_t c0 = 0; c0 < nkb && ok; c0 += a.drain_kb, ++cc) {
                     const uint32_t b = (uint32_t)(cc & 1);
                     if (!wait_bar(&acc_empty[b], ((uint32_t)(cc >> 1) & 1) ^ 1, abort_flag, st, 2)) {
                         ok = false;
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + b * g::NMAX;
-                    const uint32_t c1 = min(nkb, c0 + g::DRAIN_KB);
+                    const uint32_t c1 = min(nkb, c0 + a.drain_kb);
                     for (uint32_t k = c0; k < c1; ++k, ++kc) {
                         const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
                         if (!wait_bar(&full[s], r & 1, abort_flag, st, 3) ||
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             for (uint32_t p = 0; p < a.ppt; ++p)
                 lab_rows[p * g::BM + row] = p < nlab ? __ldg(lsrc + (uint64_t)p * a.n_pad) : (uint8_t)0;
             const uint32_t nkb = NB - 2 * I;
-            for (uint32_t c0 = 0; c0 < nkb; c0 += g::DRAIN_KB, ++cc) {
+            for (uint32_t c0 = 0; c0 < nkb; c0 += a.drain_kb, ++cc) {
                 const uint32_t b = (uint32_t)(cc & 1);
                 if (!wait_bar(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
                 tc_fence_after();
@@ -570,6 +573,12 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     a.ppt = gp.perms_per_tile;
     a.N = (a.ppt * pr.K + 15) / 16 * 16;
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
+    // accumulation length in TMEM between FP64 drains (tuning/testing override)
+    a.drain_kb = g::DRAIN_KB;
+    if (const char* env = getenv("PERMANOVA_GEMM_DRAIN")) {
+        const int v = atoi(env);
+        if (v >= 1 && v <= 4096) a.drain_kb = (uint32_t)v;
+    }
     if (a.ppt == 0 || pr.K > 256 || pr.label_type != LABEL_U8) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g::SMEM_ALLOC);

@@ -188,7 +188,11 @@ def test_permanova_test_matches_oracle(ctx, n, K, P, seed):
     sW = out_sW.cpu().numpy()
     np.testing.assert_allclose(sW, ref["s_W"], rtol=RTOL)
     assert abs(res["s_T"] - ref["s_T"]) <= RTOL * ref["s_T"]
-    assert abs(res["F_obs"] - ref["F"][0]) <= RTOL * abs(ref["F"][0])
+    # F = c (s_T - s_W) / s_W: a relative error e in s_W moves F by kappa * e with
+    # kappa = s_T / (s_T - s_W) (>> 1 when groups barely differ), so F is held to
+    # the s_W tolerance times its condition number.
+    kappa = ref["s_T"] / (ref["s_T"] - ref["s_W"][0])
+    assert abs(res["F_obs"] - ref["F"][0]) <= RTOL * max(1.0, kappa) * abs(ref["F"][0])
     # exceedance counts are exact outside the ambiguity band |s_W - s_W_obs| <= 1e-5 s_W_obs
     band = np.abs(ref["s_W"][1:] - ref["s_W"][0]) <= RTOL * ref["s_W"][0]
     if not band.any():

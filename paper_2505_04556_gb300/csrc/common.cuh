@@ -57,12 +57,18 @@ struct SWProblem {
     int label_type;
     uint32_t K;
     uint64_t P;
-    const double* w;   // inv_group_sizes widened to FP64 (device)
+    const double* w;       // inv_group_sizes widened to FP64 (device)
     double* out;
+    const float2* wsplit;  // the same weights as FP32 hi + lo pairs (hi + lo = w to ~2^-48)
 };
 
-// inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
-cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t s);
+// Weights for the kernels: out_d[k] = in_f ? (double)in_f[k] : out_d[k] (in
+// place), and out_split[k] = (hi, lo) with hi = fp32(w), lo = fp32(w - hi).
+cudaError_t launch_widen(const float* in_f, uint32_t K, double* out_d, float2* out_split,
+                         cudaStream_t s);
+
+// Sets the calling thread's error text (returned by permanova_last_error).
+void set_last_error(const char* msg);
 
 // Count of kernels the library has launched (all contexts); launchers return
 // launched(k) after issuing k kernels.
@@ -111,6 +117,10 @@ struct GemmPlan {
 bool gemm_available();
 GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P);
 size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t P);
+// label rows -> (tile, k-block) blocks of uint8 codes read by the GEMM kernel
+size_t gemm_label_bytes(const GemmPlan& gp);
+cudaError_t launch_repack_gemm(const void* in, int in_type, uint32_t n, uint64_t P, uint32_t K,
+                               const GemmPlan& gp, void* out, DevStatus* st, cudaStream_t s);
 // D^2 -> BF16 hi/lo operand tiles in the scratch
 cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s);
 // the tensor-core kernel: partials is gp.n_bands x P

@@ -59,9 +59,9 @@ constexpr uint32_t B_BYTES = NMAX * BK * 2;               // 32 KB
 constexpr uint32_t LAB_BYTES = PPT_MAX * BK;              // 4 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES + LAB_BYTES;   // 68 KB
 constexpr uint32_t OFF_LABROWS = NST * STAGE_BYTES;
-constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][PPT_MAX] double
-constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * PPT_MAX * 8;
-constexpr uint32_t OFF_W = OFF_ACC64 + PPT_MAX * 8;               // [256] double
+constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][NMAX] float
+constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * NMAX * 4;        // [NMAX] double
+constexpr uint32_t OFF_W = OFF_ACC64 + NMAX * 8;                  // [256] double
 constexpr uint32_t OFF_BAR = OFF_W + 256 * 8;
 constexpr uint32_t N_BARS = 3 * NST + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
@@ -153,6 +153,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Butterfly reduce-scatter: lane l returns sum over the warp's 32 lanes of
+// v[l].  Five exchange steps (16, 8, 4, 2, 1 values), a fixed summation tree.
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], uint32_t lane) {
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool upper = (lane & (uint32_t)half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float send = upper ? v[k] : v[k + half];
+            const float keep = upper ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0];
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
@@ -272,6 +288,58 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
 }
 
 // ---------------------------------------------------------------------------
+// label blocks: for label-row tile q (ppt rows) and k-block kb (64 columns),
+// one contiguous block of ppt x 64 uint8 labels, blocks ordered (q, kb);
+// rows beyond P and columns beyond n hold 0.  Labels >= K raise DEV_BAD_LABEL
+// and are clamped to K-1.
+// ---------------------------------------------------------------------------
+template <typename Lin>
+__global__ void k_repack_gemm(const Lin* __restrict__ in, uint32_t n, uint64_t P, uint32_t K,
+                              uint32_t ppt, uint32_t NB, uint64_t n_blocks, uint8_t* __restrict__ out,
+                              DevStatus* st) {
+    const uint32_t bytes = ppt * g::BK;
+    for (uint64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+        const uint64_t q = b / NB;
+        const uint32_t kb = (uint32_t)(b % NB);
+        uint8_t* dst = out + b * bytes;
+        for (uint32_t e = threadIdx.x; e < bytes; e += blockDim.x) {
+            const uint32_t pl = e / g::BK, c = e % g::BK;
+            const uint64_t p = q * ppt + pl;
+            const uint32_t j = kb * g::BK + c;
+            uint32_t lab = 0;
+            if (p < P && j < n) {
+                lab = (uint32_t)in[p * n + j];
+                if (lab >= K) {
+                    raise_status(st, DEV_BAD_LABEL, 2u, (unsigned long long)(p * n + j));
+                    lab = K - 1;
+                }
+            }
+            dst[e] = (uint8_t)lab;
+        }
+    }
+}
+
+size_t gemm_label_bytes(const GemmPlan& gp) {
+    return (size_t)gp.n_ptiles * gp.perms_per_tile * gp.n_pad;
+}
+
+cudaError_t launch_repack_gemm(const void* in, int in_type, uint32_t n, uint64_t P, uint32_t K,
+                               const GemmPlan& gp, void* out, DevStatus* st, cudaStream_t s) {
+    const uint32_t NB = 2 * gp.n_bands;
+    const uint64_t n_blocks = gp.n_ptiles * NB;
+    const unsigned blocks = (unsigned)(n_blocks < 152ull * 16 ? n_blocks : 152ull * 16);
+    uint8_t* o = (uint8_t*)out;
+    const uint32_t ppt = gp.perms_per_tile;
+    if (in_type == LABEL_U8)
+        k_repack_gemm<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t*)in, n, P, K, ppt, NB, n_blocks, o, st);
+    else if (in_type == LABEL_U16)
+        k_repack_gemm<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)in, n, P, K, ppt, NB, n_blocks, o, st);
+    else
+        k_repack_gemm<int32_t><<<blocks, 256, 0, s>>>((const int32_t*)in, n, P, K, ppt, NB, n_blocks, o, st);
+    return launched(1);
+}
+
+// ---------------------------------------------------------------------------
 // the persistent tensor-core kernel
 // ---------------------------------------------------------------------------
 struct GemmArgs {
@@ -321,7 +389,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
     uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
-    double* red = reinterpret_cast<double*>(sm + g::OFF_RED);    // [2][4][PPT_MAX]
+    float* red = reinterpret_cast<float*>(sm + g::OFF_RED);      // [2][4][NMAX]
     double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);
     double* wtab = reinterpret_cast<double*>(sm + g::OFF_W);
 
@@ -368,21 +436,21 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             uint64_t kc = 0;
             int64_t last_round[g::NST] = {-1, -1, -1};
             bool ok = true;
+            const uint32_t lab_bytes = a.ppt * g::BK;
             for (uint64_t u = blockIdx.x; u < n_units && ok && !*abort_flag; u += gridDim.x) {
                 const uint32_t I = (uint32_t)(u / a.n_ptiles);
-                const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
-                const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
+                const uint64_t q = u % a.n_ptiles;
+                const uint8_t* lab_tile = a.labels + q * NB * (uint64_t)lab_bytes;
                 const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
                 for (uint32_t kb = 2 * I; kb < NB; ++kb, ++kc, tile += g::TILE_BYTES) {
                     const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
                     if (!wait_bar(&empty[s], (r & 1) ^ 1, abort_flag, st, 1)) { ok = false; break; }
                     uint8_t* stg = sm + s * g::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[s], g::A_BYTES + nlab * g::BK);
+                    mbar_arrive_expect_tx(&full[s], g::A_BYTES + lab_bytes);
                     bulk_g2s(stg, tile, g::A_BYTES, &full[s]);
-                    const uint8_t* lsrc = a.labels + p0 * a.n_pad + (uint64_t)kb * g::BK;
-                    for (uint32_t p = 0; p < nlab; ++p)
-                        bulk_g2s(stg + g::A_BYTES + g::B_BYTES + p * g::BK, lsrc + (uint64_t)p * a.n_pad,
-                                 g::BK, &full[s]);
+                    // the tile's label slice for this k-block is one contiguous block
+                    bulk_g2s(stg + g::A_BYTES + g::B_BYTES, lab_tile + (uint64_t)kb * lab_bytes, lab_bytes,
+                             &full[s]);
                     last_round[s] = r;
                 }
             }
@@ -440,65 +508,103 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         const uint32_t q4 = warp - 4;              // TMEM lane quarter
         const uint32_t row = q4 * 32 + lane;       // row within the band
         const uint32_t K = a.K;
+        const uint32_t used = a.ppt * K;           // accumulator columns that carry a (p, g)
+        // the two accumulator columns this thread finalises, and their group weights
+        const uint32_t cA = et, cB = et + 128;
+        const double wA = cA < used ? wtab[cA % K] : 0.0;
+        const double wB = cB < used ? wtab[cB % K] : 0.0;
+        double accA = 0.0, accB = 0.0;
         uint64_t cc = 0;
         uint32_t epi_phase = 0;
         bool ok = true;
-        for (uint32_t p = et; p < g::PPT_MAX; p += 128) acc64[p] = 0.0;
         for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
             const uint32_t I = (uint32_t)(u / a.n_ptiles);
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
-            // this row's labels for the tile's label rows
-            const uint8_t* lsrc = a.labels + p0 * a.n_pad + (uint64_t)I * g::BM + row;
-            for (uint32_t p = 0; p < a.ppt; ++p)
-                lab_rows[p * g::BM + row] = p < nlab ? __ldg(lsrc + (uint64_t)p * a.n_pad) : (uint8_t)0;
+            // the band's row labels for the tile's label rows: k-blocks 2I and 2I+1 of
+            // the tile's label blocks, loaded cooperatively (16 bytes per thread-step)
+            {
+                const uint32_t lab_bytes = a.ppt * g::BK;
+                const uint8_t* lb = a.labels + ((u % a.n_ptiles) * NB + 2ull * I) * lab_bytes;
+                const uint32_t per_half = a.ppt * (g::BK / 16);
+                for (uint32_t idx = et; idx < 2 * per_half; idx += 128) {
+                    const uint32_t h = idx / per_half, rem = idx - h * per_half;
+                    const uint32_t p = rem / (g::BK / 16), c16 = rem % (g::BK / 16);
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(lb + h * lab_bytes + p * g::BK + c16 * 16));
+                    *reinterpret_cast<uint4*>(lab_rows + p * g::BM + h * g::BK + c16 * 16) = v;
+                }
+                mbar_arrive(epi_bar);
+                if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 10, false)) { ok = false; break; }
+                ++epi_phase;
+            }
+            // this row's selection masks for the unit: bit k of msk[grp] is set when
+            // accumulator column c = 32 grp + k is (p, g_p(row)) of a label row p
+            uint32_t msk[g::NMAX / 32];
+            {
+                uint32_t p = 0, gcol = 0, lab = lab_rows[row];
+#pragma unroll
+                for (int grp = 0; grp < g::NMAX / 32; ++grp) {
+                    uint32_t m = 0;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        if (32u * grp + k < used) {
+                            m |= (gcol == lab ? 1u : 0u) << k;
+                            if (++gcol == K) {
+                                gcol = 0;
+                                ++p;
+                                lab = p < a.ppt ? lab_rows[p * g::BM + row] : 0u;
+                            }
+                        }
+                    }
+                    msk[grp] = m;
+                }
+            }
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t c0 = 0; c0 < nkb; c0 += a.drain_kb, ++cc) {
                 const uint32_t b = (uint32_t)(cc & 1);
                 if (!wait_bar(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
                 tc_fence_after();
-                double* redc = red + (cc & 1) * 4 * g::PPT_MAX;
-                // walk the accumulator columns c = p*K + gcol; keep column g_p(row) of row p
-                uint32_t p = 0, gcol = 0;
-                uint32_t lab = lab_rows[row];
-                float sel = 0.f;
+                float* redc = red + (cc & 1) * 4 * g::NMAX;
                 const uint32_t taddr = tmem + ((q4 * 32u) << 16) + b * g::NMAX;
-                for (uint32_t grp = 0; grp < a.N / 32; ++grp) {
-                    uint32_t r[32];
-                    __syncwarp();
-                    tmem_ld32(taddr + grp * 32, r);
-                    tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        if (p < a.ppt) {
-                            if (gcol == lab) sel = __uint_as_float(r[k]);
-                            if (++gcol == K) {
-                                double v = (double)sel * wtab[lab];
+                for (int grp = 0; grp < g::NMAX / 32; ++grp) {
+                    if (32u * grp < a.N) {
+                        uint32_t r[32];
+                        __syncwarp();
+                        tmem_ld32(taddr + grp * 32, r);
+                        tmem_ld_wait();
+                        float v[32];
 #pragma unroll
-                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                                if (lane == 0) redc[q4 * g::PPT_MAX + p] = v;
-                                ++p;
-                                gcol = 0;
-                                sel = 0.f;
-                                lab = p < a.ppt ? lab_rows[p * g::BM + row] : 0u;
-                            }
-                        }
+                        for (int k = 0; k < 32; ++k) v[k] = (msk[grp] >> k) & 1u ? __uint_as_float(r[k]) : 0.f;
+                        // column 32 grp + lane summed over the warp's 32 rows
+                        redc[q4 * g::NMAX + 32 * grp + lane] = reduce_scatter32(v, lane);
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[b]);
-                // the four warps' row sums of this chunk, added in a fixed order
+                // the four warps' column sums of this chunk, added in a fixed order,
+                // weighted and accumulated in FP64
                 mbar_arrive(epi_bar);
                 if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 9, false)) { ok = false; break; }
                 ++epi_phase;
-                for (uint32_t pp = et; pp < a.ppt; pp += 128)
-                    acc64[pp] += (redc[pp] + redc[g::PPT_MAX + pp]) +
-                                 (redc[2 * g::PPT_MAX + pp] + redc[3 * g::PPT_MAX + pp]);
+                if (cA < used)
+                    accA += (double)((redc[cA] + redc[g::NMAX + cA]) + (redc[2 * g::NMAX + cA] + redc[3 * g::NMAX + cA])) * wA;
+                if (cB < used)
+                    accB += (double)((redc[cB] + redc[g::NMAX + cB]) + (redc[2 * g::NMAX + cB] + redc[3 * g::NMAX + cB])) * wB;
             }
             if (!ok) break;
-            for (uint32_t pp = et; pp < a.ppt; pp += 128) {
-                if (pp < nlab) a.partials[(uint64_t)I * a.P + p0 + pp] = acc64[pp];
-                acc64[pp] = 0.0;
+            // per label row: the sum of its K columns, in group order
+            acc64[cA] = accA;
+            acc64[cB] = accB;
+            accA = 0.0;
+            accB = 0.0;
+            mbar_arrive(epi_bar);
+            if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 11, false)) { ok = false; break; }
+            ++epi_phase;
+            for (uint32_t pp = et; pp < nlab; pp += 128) {
+                double t = 0.0;
+                for (uint32_t gg = 0; gg < K; ++gg) t += acc64[pp * K + gg];
+                a.partials[(uint64_t)I * a.P + p0 + pp] = t;
             }
         }
     } else if (warp >= 8) {

@@ -133,15 +133,18 @@ int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, cons
     off = align_up(off + (size_t)L->part_rows * P * sizeof(double));
     if (L->repack) {
         L->lab_off = off;
-        off = align_up(off + (size_t)L->lstride * P * label_bytes(L->code_type));
+        const size_t lab = form == PERMANOVA_FORM_GEMM
+                               ? gemm_label_bytes(gemm_plan(n, K, P))
+                               : (size_t)L->lstride * P * label_bytes(L->code_type);
+        off = align_up(off + lab);
     }
     if (form == PERMANOVA_FORM_GEMM) {
         const GemmPlan gp = gemm_plan(n, K, P);
         L->gemm_off = off;
         off = align_up(off + gemm_scratch_bytes(gp, P));
     }
-    L->w_off = off;
-    off = align_up(off + (size_t)K * sizeof(double));
+    L->w_off = off;   // K doubles, then K float2 (fp32 hi/lo split)
+    off = align_up(align_up(off + (size_t)K * sizeof(double)) + (size_t)K * sizeof(float2));
     L->total = off;
     return PERMANOVA_OK;
 }
@@ -217,13 +220,16 @@ void profile_clear(permanova_ctx* ctx) {
 
 // The s_W path on device buffers; the arena is already large enough.
 // `wf` (device fp32 inv_group_sizes) is widened into the layout's FP64 slot;
-// with wf == NULL the slot already holds the weights.
+// with wf == NULL the slot already holds the FP64 weights.  Both paths also
+// write the fp32 hi/lo split used by the perm-block kernel.
 int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s) {
     char* base = static_cast<char*>(ctx->arena);
     double* partials = reinterpret_cast<double*>(base + L.part_off);
     double* wd = reinterpret_cast<double*>(base + L.w_off);
-    if (wf) CK(launch_widen(wf, pr.K, wd, s), "widen weights");
+    float2* ws = reinterpret_cast<float2*>(base + align_up(L.w_off + (size_t)pr.K * sizeof(double)));
+    CK(launch_widen(wf, pr.K, wd, ws, s), "widen weights");
     pr.w = wd;
+    pr.wsplit = ws;
     SWProblem q = pr;
     if (L.form == PERMANOVA_FORM_BRUTE) {
         CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K, ctx->status, s),
@@ -236,9 +242,14 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
     } else {
         if (L.repack) {
             void* codes = base + L.lab_off;
-            CK(launch_repack_labels(pr.labels, pr.label_type, pr.n, pr.P, pr.K, codes, L.code_type,
-                                    L.lstride, ctx->status, s),
-               "repack labels");
+            if (L.form == PERMANOVA_FORM_GEMM)
+                CK(launch_repack_gemm(pr.labels, pr.label_type, pr.n, pr.P, pr.K, gemm_plan(pr.n, pr.K, pr.P),
+                                      codes, ctx->status, s),
+                   "repack labels");
+            else
+                CK(launch_repack_labels(pr.labels, pr.label_type, pr.n, pr.P, pr.K, codes, L.code_type,
+                                        L.lstride, ctx->status, s),
+                   "repack labels");
             q.labels = codes;
             q.label_type = L.code_type;
         } else {
@@ -285,6 +296,8 @@ int read_status(permanova_ctx* ctx, cudaStream_t s) {
 }
 
 }  // namespace
+
+void pmn::set_last_error(const char* msg) { tl_err = msg; }
 
 extern "C" {
 

@@ -138,6 +138,30 @@ int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uin
                       const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
                       const float *inv_group_sizes, double *out_sW, void *stream);
 
+/* permanova_sW for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment variant.  Callers that cannot call
+ * cudaMalloc include code recording a CUDA graph that must not contain
+ * allocations, plugins whose host framework owns every device allocation,
+ * and processes pinned to a fixed memory pool with no headroom.
+ * It needs no context and allocates nothing: it runs the brute-force kernels
+ * with their scratch (FP64 partial sums, FP64 weights, the device error word)
+ * in one fixed 8 MiB device array that the library keeps resident on every
+ * GPU that loads it, until the process exits.
+ *   Arguments as permanova_sW (DEVICE mat, groupings, inv_group_sizes,
+ *   out_sW; the current CUDA device is used).
+ *   Limits: n_perms * 8 bytes must fit in the array after the error word and
+ *   the weights (1,048,512 label rows with n_groups <= 32); larger calls
+ *   return PERMANOVA_EINVAL with a message, before any work is queued.
+ *   The first call on a device looks up the array's device address; make
+ *   that first call outside any stream capture.
+ *   The call synchronises `stream` and reports a label >= n_groups as
+ *   PERMANOVA_EINVAL.  All calls on a device share the array: calls whose work
+ *   overlaps on the GPU (other streams, other host threads) race, so callers
+ *   must serialise them.  Error text: permanova_last_error(NULL). */
+int permanova_sW_noalloc(const float *mat, uint32_t n_dims, uint64_t ld, const void *groupings,
+                         int label_type, uint32_t n_groups, uint64_t n_perms,
+                         const float *inv_group_sizes, double *out_sW, void *stream);
+
 /* Wait for `stream`, then report (and clear) any device error word raised by
  * earlier asynchronous calls on this context.  Returns OK, EINVAL (invalid
  * label), ETIMEOUT or ECUDA. */

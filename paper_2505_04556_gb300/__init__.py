@@ -102,6 +102,8 @@ def load(path: str | None = None):
         lib.permanova_test.argtypes = [vp, vp, u32, u64, vp, u32, u64, u64,
                                        ctypes.POINTER(permanova_result), vp, vp]
         lib.permanova_test.restype = i32
+        lib.permanova_sW_noalloc.argtypes = [vp, u32, u64, vp, i32, u32, u64, vp, vp, vp]
+        lib.permanova_sW_noalloc.restype = i32
         lib.permanova_profile_enable.argtypes = [vp, i32]
         lib.permanova_profile_enable.restype = i32
         lib.permanova_profile_read.argtypes = [vp, ctypes.POINTER(permanova_profile_t)]
@@ -203,6 +205,16 @@ def permanova_sW_host(ctx, mat, n_dims: int, ld: int, groupings, label_type: int
                                   int(label_type), int(n_groups), int(n_perms),
                                   _ptr(inv_group_sizes), _ptr(out_sW), _stream(stream))
     _check(ctx, rc)
+
+
+def permanova_sW_noalloc(mat, n_dims: int, ld: int, groupings, label_type: int, n_groups: int,
+                         n_perms: int, inv_group_sizes, out_sW, stream=None) -> None:
+    """s_W with no device allocation (fixed 8 MiB library-resident scratch; for
+    callers that must not call cudaMalloc).  Synchronises the stream."""
+    rc = load().permanova_sW_noalloc(_ptr(mat), int(n_dims), int(ld), _ptr(groupings),
+                                     int(label_type), int(n_groups), int(n_perms),
+                                     _ptr(inv_group_sizes), _ptr(out_sW), _stream(stream))
+    _check(None, rc)
 
 
 def permanova_sync(ctx, stream=None) -> None:

@@ -1,0 +1,123 @@
+// s_W without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code running inside a CUDA stream
+// capture that must not add allocation nodes, plugins of host frameworks that
+// own every device allocation themselves (and forbid others), and processes
+// that run with a fixed memory pool and no headroom.  For them,
+// permanova_sW_noalloc runs the brute-force s_W kernels with their scratch
+// (FP64 partial sums, FP64 weights, the device error word) in one fixed
+// file-scope device array instead of context memory.  It needs no context.
+//
+// The array is NOALLOC_BYTES (8 MiB) and stays resident on every GPU that
+// loads this library until the process exits.  All calls on a device share
+// it, so calls whose work overlaps on that GPU (different streams or host
+// threads) race; callers must serialise them.  Each call clears the error
+// word before use and overwrites the partials and weights it reads.
+#include "../../include/permanova.h"
+#include "common.cuh"
+
+#include <cstdio>
+#include <mutex>
+
+namespace pmn {
+
+constexpr size_t NOALLOC_BYTES = 8u << 20;
+constexpr size_t NOALLOC_STATUS = 0;       // DevStatus
+constexpr size_t NOALLOC_W = 256;          // K doubles
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the first call on a device must therefore not be inside a
+// stream capture).
+static cudaError_t noalloc_base(int dev, void** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace pmn
+
+using namespace pmn;
+
+extern "C" int permanova_sW_noalloc(const float* mat, uint32_t n, uint64_t ld, const void* groupings,
+                                    int label_type, uint32_t K, uint64_t P,
+                                    const float* inv_group_sizes, double* out_sW, void* stream) {
+    char msg[256];
+    auto err = [&](int code, const char* text) {
+        set_last_error(text);   // readable through permanova_last_error(NULL)
+        return code;
+    };
+    if (!mat || !groupings || !inv_group_sizes || !out_sW) return err(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (n < 2) return err(PERMANOVA_EINVAL, "n_dims must be >= 2");
+    if (ld < n) return err(PERMANOVA_EINVAL, "ld < n_dims");
+    if (K == 0 || P == 0) return err(PERMANOVA_EINVAL, "n_groups and n_perms must be >= 1");
+    if (label_type != LABEL_I32 && label_type != LABEL_U16 && label_type != LABEL_U8)
+        return err(PERMANOVA_EINVAL, "unknown label type");
+    if ((label_type == LABEL_U8 && K > 256) || (label_type == LABEL_U16 && K > 65536))
+        return err(PERMANOVA_EINVAL, "label type too narrow for n_groups");
+    // capacity: K weights after the status word, then chunks x P partials
+    const size_t part_off = (NOALLOC_W + (size_t)K * sizeof(double) + 255) / 256 * 256;
+    if (part_off >= NOALLOC_BYTES) {
+        snprintf(msg, sizeof msg, "n_groups = %u exceeds the no-allocation scratch (%zu bytes)", K,
+                 NOALLOC_BYTES);
+        return err(PERMANOVA_EINVAL, msg);
+    }
+    const uint64_t max_rows = (NOALLOC_BYTES - part_off) / ((uint64_t)P * sizeof(double));
+    if (max_rows < 1) {
+        snprintf(msg, sizeof msg,
+                 "n_perms = %llu exceeds the no-allocation scratch (at most %zu label rows per call)",
+                 (unsigned long long)P, (NOALLOC_BYTES - part_off) / sizeof(double));
+        return err(PERMANOVA_EINVAL, msg);
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return err(PERMANOVA_ECUDA, "no current CUDA device");
+    void* base = nullptr;
+    cudaError_t e = noalloc_base(dev, &base);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return err(PERMANOVA_ECUDA, msg);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* b = static_cast<unsigned char*>(base);
+    DevStatus* st = reinterpret_cast<DevStatus*>(b + NOALLOC_STATUS);
+    double* wd = reinterpret_cast<double*>(b + NOALLOC_W);
+    double* partials = reinterpret_cast<double*>(b + part_off);
+    uint32_t chunks = brute_chunks(n, 0);
+    if ((uint64_t)chunks > max_rows) chunks = (uint32_t)max_rows;
+
+    SWProblem pr{mat, n, ld, groupings, label_type, K, P, wd, out_sW};
+    if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) == cudaSuccess &&
+        (e = launch_widen(inv_group_sizes, K, wd, nullptr, s)) == cudaSuccess &&
+        (e = launch_validate_labels(groupings, label_type, (uint64_t)n * P, K, st, s)) == cudaSuccess &&
+        (e = launch_brute(pr, chunks, partials, st, s)) == cudaSuccess &&
+        (e = launch_reduce_rows(partials, chunks, P, out_sW, s)) == cudaSuccess) {
+        DevStatus h{};
+        e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) {
+            if (h.code == DEV_BAD_LABEL) {
+                snprintf(msg, sizeof msg, "label >= n_groups at flat index %llu", h.info);
+                return err(PERMANOVA_EINVAL, msg);
+            }
+            if (h.code != DEV_OK) return err(PERMANOVA_ECUDA, "device error");
+            return PERMANOVA_OK;
+        }
+    }
+    cudaGetLastError();
+    snprintf(msg, sizeof msg, "CUDA error: %s", cudaGetErrorString(e));
+    return err(PERMANOVA_ECUDA, msg);
+}

@@ -205,8 +205,93 @@ def traffic_per_launch(form: str, evals: float) -> float | None:
     return None
 
 
+def combine_ranks(elapsed: float, units: float) -> tuple[float, float]:
+    """Across torch.distributed ranks: the max elapsed time and the summed
+    units (replicas: no data is exchanged, only these two numbers)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed, units
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Label-row seed of a rank: ranks draw disjoint streams of label rows."""
+    return base + 1000 * rank
+
+
+def serving_bench(args) -> None:
+    """Serving workload: 64 resident matrices (n log-uniform in 500..30,000,
+    Gaussian points in R^16/R^32, Euclidean fp32), each with 1-20 categorical
+    factors (K uniform in 2..12, Dirichlet(2) sizes, each group >= 2), tests of
+    999 or 9,999 permutations (even odds) arriving as a Poisson process at
+    ``--rate`` tests/s for ``--duration`` seconds.  Prints tests/s and p50/p99
+    latency (arrival to result)."""
+    import torch
+    import paper_2505_04556_gb300 as pm
+    from paper_2505_04556_gb300.serve import Request, Server
+    pm.build()
+    rng = np.random.default_rng(5005)
+    mats, factors = {}, {}
+    for m in range(64):
+        n = int(round(math.exp(rng.uniform(math.log(500), math.log(30000)))))
+        dim = 16 if m % 2 == 0 else 32
+        X = rng.standard_normal((n, dim))
+        cfg = {"kind": "euclid"}
+        mats[m] = synth.recipe_matrix_device(cfg, X)
+        fl = []
+        for _ in range(int(rng.integers(1, 21))):
+            K = int(rng.integers(2, 13))
+            sizes = synth.largest_remainder_sizes(n, rng.dirichlet(2.0 * np.ones(K)), min_size=2)
+            fl.append((synth.observed_labels(sizes, int(rng.integers(1 << 30))), K))
+        factors[m] = fl
+    torch.cuda.synchronize()
+    srv = Server(mats, n_slots=args.slots)
+    reqs = []
+    t0 = time.perf_counter()
+    t_next = t0
+    k = 0
+    while True:
+        t_next += rng.exponential(1.0 / args.rate)
+        if t_next - t0 > args.duration:
+            break
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+        m = int(rng.integers(64))
+        lab, K = factors[m][int(rng.integers(len(factors[m])))]
+        P = 999 if rng.random() < 0.5 else 9999
+        reqs.append(srv.submit(Request(m, lab, K, P, seed=10_000 + k)))
+        k += 1
+    for r in reqs:
+        r.done.wait(600)
+    wall = max(r.t_done for r in reqs) - t0
+    srv.close()
+    s = Server.summarize(reqs, wall)
+    evals = sum(mats[r.matrix_id].shape[0] * (mats[r.matrix_id].shape[0] - 1) / 2 * (r.n_perms + 1)
+                for r in reqs if r.error is None)
+    line = {"metric": "served PERMANOVA tests/s (p50/p99 latency)", "value": s.get("tests_per_s"),
+            "unit": "tests/s", "p50_s": s.get("p50_s"), "p99_s": s.get("p99_s"),
+            "tests": s.get("tests"), "errors": s.get("errors"), "offered_rate": args.rate,
+            "duration_s": args.duration, "slots": args.slots,
+            "pair_perm_evals_per_s": evals / wall, "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic",
+            "config": {"workload": "serving-64", "matrices": 64, "n_range": [500, 30000],
+                       "perms": [999, 9999], "K_range": [2, 12], "arrivals": "Poisson"},
+            "gpu": torch.cuda.get_device_name(0)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--serving", action="store_true")
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -218,6 +303,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.serving:
+        serving_bench(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -278,7 +366,7 @@ def main():
     # ---- inputs resident in HBM before timing ----
     D = synth.recipe_matrix_device(cfg, X, device=f"cuda:{dev}")
     n_rows = min(P, (args.warmup + args.steps) * B)
-    lab = synth.device_label_rows(cfg["labels"], n_rows, cfg["seed_perms"] + 1000 * rank,
+    lab = synth.device_label_rows(cfg["labels"], n_rows, rank_seed(cfg["seed_perms"], rank),
                                   device=f"cuda:{dev}", dtype=torch.uint8)
     w = torch.from_numpy(cfg["w"]).to(f"cuda:{dev}")
     out = torch.empty(n_rows, dtype=torch.float64, device=f"cuda:{dev}")
@@ -317,17 +405,7 @@ def main():
     prof = pm.permanova_profile_read(ctx.handle)
     pm.permanova_profile_enable(ctx.handle, False)
     pm.permanova_sync(ctx.handle, stream)
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        import torch.distributed as dist
-        tms = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-        ms = float(tms.item())
-        rd = torch.tensor([rows_done], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(rd, op=dist.ReduceOp.SUM)
-        rows_total = float(rd.item())
-    else:
-        rows_total = float(rows_done)
+    ms, rows_total = combine_ranks(t_start.elapsed_time(t_end), float(rows_done))
     value = pairs * rows_total / (ms / 1e3)
 
     # ---- dominant kernel roofline ----
@@ -361,13 +439,8 @@ def main():
         for _ in range(args.e2e_steps):
             e2e_step()
         barrier()
-        te = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([te], dtype=torch.float64, device=f"cuda:{dev}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": pairs * B * args.e2e_steps * world / te, "unit": UNIT,
+        te, rows_e2e = combine_ranks(time.perf_counter() - t0, float(B * args.e2e_steps))
+        e2e = {"value": pairs * rows_e2e / te, "unit": UNIT,
                "h2d_bytes_per_step": int(n * n * 4 + B * n + K * 4),
                "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps,
                "api": "permanova_sW_host (pinned host D, labels, weights, results)"}

@@ -59,13 +59,10 @@ struct SWProblem {
     uint64_t P;
     const double* w;       // inv_group_sizes widened to FP64 (device)
     double* out;
-    const float2* wsplit;  // the same weights as FP32 hi + lo pairs (hi + lo = w to ~2^-48)
 };
 
-// Weights for the kernels: out_d[k] = in_f ? (double)in_f[k] : out_d[k] (in
-// place), and out_split[k] = (hi, lo) with hi = fp32(w), lo = fp32(w - hi).
-cudaError_t launch_widen(const float* in_f, uint32_t K, double* out_d, float2* out_split,
-                         cudaStream_t s);
+// inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
+cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t s);
 
 // Sets the calling thread's error text (returned by permanova_last_error).
 void set_last_error(const char* msg);

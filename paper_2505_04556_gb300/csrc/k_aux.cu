@@ -140,22 +140,14 @@ cudaError_t launch_reduce_rows(const double* partials, uint32_t rows, uint64_t P
     return launched(1);
 }
 
-__global__ void k_widen(const float* __restrict__ in_f, uint32_t K, double* out_d,
-                        float2* __restrict__ out_split) {
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-        const double w = in_f ? (double)in_f[k] : out_d[k];
-        out_d[k] = w;
-        if (out_split) {
-            const float hi = (float)w;
-            out_split[k] = make_float2(hi, (float)(w - (double)hi));
-        }
-    }
+__global__ void k_widen(const float* __restrict__ in, uint32_t K, double* __restrict__ out) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+        out[k] = (double)in[k];
 }
 
-cudaError_t launch_widen(const float* in_f, uint32_t K, double* out_d, float2* out_split,
-                         cudaStream_t s) {
+cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t s) {
     const unsigned blocks = (K + 255) / 256 < 64 ? (K + 255) / 256 : 64;
-    k_widen<<<blocks, 256, 0, s>>>(in_f, K, out_d, out_split);
+    k_widen<<<blocks, 256, 0, s>>>(in, K, out);
     return launched(1);
 }
 

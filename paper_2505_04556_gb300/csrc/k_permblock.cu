@@ -14,7 +14,8 @@
 //   * D^2 is read from shared memory with 128-bit broadcast loads;
 //   * as in Algorithm 2, the row segment is summed unweighted and multiplied
 //     by w_{g_p(i)} once.  Row segments (64 terms, four FP32 partial sums)
-//     are weighted and accumulated in FP64; the CTA writes one FP64
+//     are weighted and accumulated in FP64 (one DFMA per 64 evaluations);
+//     the next row's label is fetched one row ahead; the CTA writes one FP64
 //     partial per (band, label row).
 // Labels arrive as uint8 (K <= 256) or uint16 codes whose row stride is a
 // multiple of 16 bytes, so each thread loads its 64 column labels of a full
@@ -34,6 +35,13 @@ __device__ __forceinline__ float code_u16(uint32_t word, int k) {
     return __uint_as_float(__byte_perm(word, 0x4B000000u, k ? 0x7432u : 0x7410u));
 }
 __device__ __forceinline__ float code_of(uint32_t g) { return __uint_as_float(0x4B000000u | g); }
+
+// 1.0f if a == b else 0.0f, in one compare-and-set
+__device__ __forceinline__ float select_eq(float a, float b) {
+    float d;
+    asm("set.eq.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
 
 template <typename L>
 __device__ __forceinline__ void load_col_codes(const L* __restrict__ g, uint32_t j0, float* cl);
@@ -123,18 +131,20 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
         }
         __syncthreads();
 
+        uint32_t gnext = min((uint32_t)g[r0], K - 1);
         for (uint32_t r = 0; r < rows; ++r) {
-            const uint32_t gi = min((uint32_t)g[r0 + r], K - 1);
+            const uint32_t gi = gnext;
+            if (r + 1 < rows) gnext = min((uint32_t)g[r0 + r + 1], K - 1);   // prefetch
             const float fgi = code_of(gi);
             const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
             float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c4 = 0; c4 < PB_T / 4; ++c4) {
                 const float4 dv = drow[c4];
-                const float e0 = (cl[4 * c4 + 0] == fgi) ? 1.f : 0.f;
-                const float e1 = (cl[4 * c4 + 1] == fgi) ? 1.f : 0.f;
-                const float e2 = (cl[4 * c4 + 2] == fgi) ? 1.f : 0.f;
-                const float e3 = (cl[4 * c4 + 3] == fgi) ? 1.f : 0.f;
+                const float e0 = select_eq(cl[4 * c4 + 0], fgi);
+                const float e1 = select_eq(cl[4 * c4 + 1], fgi);
+                const float e2 = select_eq(cl[4 * c4 + 2], fgi);
+                const float e3 = select_eq(cl[4 * c4 + 3], fgi);
                 a0 = __ffma2_rn(make_float2(e0, e1), make_float2(dv.x, dv.y), a0);
                 a1 = __ffma2_rn(make_float2(e2, e3), make_float2(dv.z, dv.w), a1);
             }

@@ -101,7 +101,7 @@ extern "C" int permanova_sW_noalloc(const float* mat, uint32_t n, uint64_t ld, c
 
     SWProblem pr{mat, n, ld, groupings, label_type, K, P, wd, out_sW};
     if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) == cudaSuccess &&
-        (e = launch_widen(inv_group_sizes, K, wd, nullptr, s)) == cudaSuccess &&
+        (e = launch_widen(inv_group_sizes, K, wd, s)) == cudaSuccess &&
         (e = launch_validate_labels(groupings, label_type, (uint64_t)n * P, K, st, s)) == cudaSuccess &&
         (e = launch_brute(pr, chunks, partials, st, s)) == cudaSuccess &&
         (e = launch_reduce_rows(partials, chunks, P, out_sW, s)) == cudaSuccess) {

@@ -143,8 +143,8 @@ int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, cons
         L->gemm_off = off;
         off = align_up(off + gemm_scratch_bytes(gp, P));
     }
-    L->w_off = off;   // K doubles, then K float2 (fp32 hi/lo split)
-    off = align_up(align_up(off + (size_t)K * sizeof(double)) + (size_t)K * sizeof(float2));
+    L->w_off = off;   // K doubles
+    off = align_up(off + (size_t)K * sizeof(double));
     L->total = off;
     return PERMANOVA_OK;
 }
@@ -220,16 +220,13 @@ void profile_clear(permanova_ctx* ctx) {
 
 // The s_W path on device buffers; the arena is already large enough.
 // `wf` (device fp32 inv_group_sizes) is widened into the layout's FP64 slot;
-// with wf == NULL the slot already holds the FP64 weights.  Both paths also
-// write the fp32 hi/lo split used by the perm-block kernel.
+// with wf == NULL the slot already holds the FP64 weights.
 int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s) {
     char* base = static_cast<char*>(ctx->arena);
     double* partials = reinterpret_cast<double*>(base + L.part_off);
     double* wd = reinterpret_cast<double*>(base + L.w_off);
-    float2* ws = reinterpret_cast<float2*>(base + align_up(L.w_off + (size_t)pr.K * sizeof(double)));
-    CK(launch_widen(wf, pr.K, wd, ws, s), "widen weights");
+    if (wf) CK(launch_widen(wf, pr.K, wd, s), "widen weights");
     pr.w = wd;
-    pr.wsplit = ws;
     SWProblem q = pr;
     if (L.form == PERMANOVA_FORM_BRUTE) {
         CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K, ctx->status, s),

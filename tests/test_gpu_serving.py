@@ -1,0 +1,106 @@
+"""Serving loop: continuous admission, overlapping execution, and results that
+do not depend on the traffic mix."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def matrices():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2505_04556_gb300 as pm
+    pm.build()
+    rng = np.random.default_rng(11)
+    mats, hosts = {}, {}
+    for mid, n in enumerate((300, 777, 1500)):
+        D = synth.euclidean_matrix(rng.standard_normal((n, 6)))
+        hosts[mid] = D
+        mats[mid] = torch.from_numpy(D).cuda()
+    return mats, hosts
+
+
+def _requests(hosts, seed):
+    from paper_2505_04556_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(12):
+        mid = k % len(hosts)
+        n = hosts[mid].shape[0]
+        K = int(rng.integers(2, 7))
+        sizes = synth.largest_remainder_sizes(n, rng.dirichlet(np.ones(K) * 2), min_size=2)
+        lab = synth.observed_labels(sizes, 100 + k)
+        P = int(rng.choice([99, 499]))
+        reqs.append(Request(mid, lab, K, P, seed=1000 + k))
+    return reqs
+
+
+def test_results_identical_alone_and_in_the_mix(matrices):
+    from paper_2505_04556_gb300.serve import Server
+    mats, hosts = matrices
+    # alone: one slot, one request at a time
+    alone = []
+    srv = Server(mats, n_slots=1)
+    try:
+        for r in _requests(hosts, 5):
+            srv.submit(r)
+            assert r.done.wait(120)
+            assert r.error is None, r.error
+            alone.append(r.result)
+    finally:
+        srv.close()
+    # mixed: four slots, everything submitted at once
+    srv = Server(mats, n_slots=4)
+    try:
+        reqs = _requests(hosts, 5)
+        for r in reqs:
+            srv.submit(r)
+        for r in reqs:
+            assert r.done.wait(120)
+            assert r.error is None, r.error
+        overlap = any(a.t_start < b.t_done and b.t_start < a.t_done
+                      for i, a in enumerate(reqs) for b in reqs[i + 1:])
+        assert overlap, "no two tests were in flight together"
+        for r, ref in zip(reqs, alone):
+            for key in ("s_T", "s_W_obs", "F_obs", "p_value", "n_ge", "n_perms"):
+                assert r.result[key] == ref[key], key
+        summary = Server.summarize(reqs, max(r.t_done for r in reqs) - min(r.t_arrival for r in reqs))
+        assert summary["tests"] == len(reqs) and summary["p99_s"] >= summary["p50_s"]
+    finally:
+        srv.close()
+
+
+def test_served_result_matches_oracle(matrices):
+    from paper_2505_04556_gb300.serve import Request, Server
+    mats, hosts = matrices
+    lab = synth.observed_labels([300, 277, 200], 3)
+    srv = Server(mats, n_slots=2)
+    try:
+        r = srv.submit(Request(1, lab, 3, 199, seed=77))
+        assert r.done.wait(120) and r.error is None
+    finally:
+        srv.close()
+    ref = oracle.permanova_test(hosts[1], lab, 3, 199, 77)
+    assert abs(r.result["s_W_obs"] - ref["s_W"][0]) <= 1e-5 * ref["s_W"][0]
+    band = np.abs(ref["s_W"][1:] - ref["s_W"][0]) <= 1e-5 * ref["s_W"][0]
+    if not band.any():
+        assert r.result["n_ge"] == ref["n_ge"]
+
+
+def test_oversized_request_rejected_not_run(matrices):
+    from paper_2505_04556_gb300.serve import Request, Server
+    mats, hosts = matrices
+    srv = Server(mats, n_slots=1, hbm_budget_bytes=1 << 20)
+    try:
+        r = srv.submit(Request(2, synth.observed_labels([750, 750], 1), 2, 999, seed=1))
+        assert r.done.wait(5)
+        assert r.error is not None and "budget" in r.error
+    finally:
+        srv.close()

@@ -106,6 +106,25 @@ int permanova_set_form(permanova_ctx *ctx, int form);
 /* Form the planner would use (or the forced one) for these sizes. */
 int permanova_plan_form(permanova_ctx *ctx, uint32_t n_dims, uint32_t n_groups, uint64_t n_perms);
 
+/* Autotuner: times every kernel form that can run these sizes on a sample of
+ * the given label rows (at most 4,096 rows, about 0.2 s of work), and makes
+ * the fastest the planner's choice for calls with the same log2 buckets of
+ * n_dims and n_perms and the same n_groups.  Arguments as permanova_sW (no
+ * output buffer: the sample's results go to scratch).  *out_form (optional,
+ * HOST) receives the chosen permanova_form_t.  Synchronises `stream`; errors
+ * as permanova_sW. */
+int permanova_autotune(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                       const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
+                       const float *inv_group_sizes, int *out_form, void *stream);
+
+/* CUDA graphs (1 = on, 0 = off, the default): with graphs on, a
+ * permanova_sW call on a non-default stream whose arguments and chosen form
+ * repeat an earlier call's replays the captured graph of its launches instead
+ * of launching each kernel.  Graphs are dropped when the scratch arena grows
+ * and when graphs are turned off; calls on a stream that is already being
+ * captured, and profiled calls, launch directly. */
+int permanova_set_graphs(permanova_ctx *ctx, int enable);
+
 /* Bytes of context scratch a permanova_sW call of these sizes needs under
  * `form` (AUTO = the planner's form).  0 on invalid sizes. */
 size_t permanova_scratch_bytes(permanova_ctx *ctx, int form, uint32_t n_dims, uint32_t n_groups,

@@ -102,6 +102,11 @@ def load(path: str | None = None):
         lib.permanova_test.argtypes = [vp, vp, u32, u64, vp, u32, u64, u64,
                                        ctypes.POINTER(permanova_result), vp, vp]
         lib.permanova_test.restype = i32
+        lib.permanova_autotune.argtypes = [vp, vp, u32, u64, vp, i32, u32, u64, vp,
+                                           ctypes.POINTER(i32), vp]
+        lib.permanova_autotune.restype = i32
+        lib.permanova_set_graphs.argtypes = [vp, i32]
+        lib.permanova_set_graphs.restype = i32
         lib.permanova_sW_noalloc.argtypes = [vp, u32, u64, vp, i32, u32, u64, vp, vp, vp]
         lib.permanova_sW_noalloc.restype = i32
         lib.permanova_profile_enable.argtypes = [vp, i32]
@@ -205,6 +210,20 @@ def permanova_sW_host(ctx, mat, n_dims: int, ld: int, groupings, label_type: int
                                   int(label_type), int(n_groups), int(n_perms),
                                   _ptr(inv_group_sizes), _ptr(out_sW), _stream(stream))
     _check(ctx, rc)
+
+
+def permanova_autotune(ctx, mat, n_dims: int, ld: int, groupings, label_type: int, n_groups: int,
+                       n_perms: int, inv_group_sizes, stream=None) -> int:
+    form = ctypes.c_int(0)
+    rc = load().permanova_autotune(ctx, _ptr(mat), int(n_dims), int(ld), _ptr(groupings),
+                                   int(label_type), int(n_groups), int(n_perms),
+                                   _ptr(inv_group_sizes), ctypes.byref(form), _stream(stream))
+    _check(ctx, rc)
+    return form.value
+
+
+def permanova_set_graphs(ctx, enable: bool = True) -> None:
+    _check(ctx, load().permanova_set_graphs(ctx, 1 if enable else 0))
 
 
 def permanova_sW_noalloc(mat, n_dims: int, ld: int, groupings, label_type: int, n_groups: int,

@@ -51,6 +51,7 @@ constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
 constexpr int PPT_MAX = 64;         // label rows per tile
 constexpr int NST = 3;              // pipeline stages
 constexpr int DRAIN_KB = 16;        // default k-blocks per accumulator chunk
+constexpr int PREFETCH_KB = 8;      // L2 prefetch distance along the band (k-blocks)
 constexpr int THREADS = 384;
 constexpr uint32_t PLANE_BYTES = BM * BK * 2;             // 16 KB
 constexpr uint32_t TILE_BYTES = 2 * PLANE_BYTES;          // hi + lo planes: 32 KB
@@ -63,7 +64,7 @@ constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][NMAX
 constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * NMAX * 4;        // [NMAX] double
 constexpr uint32_t OFF_W = OFF_ACC64 + NMAX * 8;                  // [256] double
 constexpr uint32_t OFF_BAR = OFF_W + 256 * 8;
-constexpr uint32_t N_BARS = 3 * NST + 6;
+constexpr uint32_t N_BARS = 4 * NST + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
 constexpr uint32_t SMEM_ALLOC = SMEM_BYTES + 1024;       // room to align the base to 1 KB
@@ -105,6 +106,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+// Warm L2 with a global range (no shared-memory destination, no completion).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -379,13 +384,15 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + g::OFF_BAR);
-    uint64_t* full = bars;                        // [NST] A tile + labels landed
+    uint64_t* full = bars;                        // [NST] A tile landed
     uint64_t* ready = bars + g::NST;              // [NST] B tile built
     uint64_t* empty = bars + 2 * g::NST;          // [NST] MMAs of the stage done
     uint64_t* acc_full = bars + 3 * g::NST;       // [2]
     uint64_t* acc_empty = bars + 3 * g::NST + 2;  // [2]
     uint64_t* epi_bar = bars + 3 * g::NST + 4;    // epilogue warps meet here once per chunk
     uint64_t* mma_done = bars + 3 * g::NST + 5;   // final commit of the MMA thread
+    uint64_t* lfull = bars + 3 * g::NST + 6;      // [NST] label slice landed (B can be built
+                                                  // while the A tile is still in flight)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
     uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
@@ -399,6 +406,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < g::NST; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&lfull[s], 1);
             mbar_init(&ready[s], 128);
             mbar_init(&empty[s], 1);
         }
@@ -446,18 +454,26 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
                     if (!wait_bar(&empty[s], (r & 1) ^ 1, abort_flag, st, 1)) { ok = false; break; }
                     uint8_t* stg = sm + s * g::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[s], g::A_BYTES + lab_bytes);
-                    bulk_g2s(stg, tile, g::A_BYTES, &full[s]);
-                    // the tile's label slice for this k-block is one contiguous block
+                    // the tile's label slice for this k-block (one contiguous block) first,
+                    // on its own barrier, so the B builders need not wait for the A tile
+                    mbar_arrive_expect_tx(&lfull[s], lab_bytes);
                     bulk_g2s(stg + g::A_BYTES + g::B_BYTES, lab_tile + (uint64_t)kb * lab_bytes, lab_bytes,
-                             &full[s]);
+                             &lfull[s]);
+                    mbar_arrive_expect_tx(&full[s], g::A_BYTES);
+                    bulk_g2s(stg, tile, g::A_BYTES, &full[s]);
                     last_round[s] = r;
+                    // pull a tile further along the band into L2, so the copies that
+                    // reach it (this CTA's and the other CTAs on the same band) hit L2
+                    if (kb + g::PREFETCH_KB < NB)
+                        bulk_prefetch_l2(tile + (uint64_t)g::PREFETCH_KB * g::TILE_BYTES, g::TILE_BYTES);
                 }
             }
             // every issued copy must land before the CTA exits
             for (int s = 0; s < g::NST; ++s)
-                if (last_round[s] >= 0)
+                if (last_round[s] >= 0) {
+                    wait_bar(&lfull[s], (uint32_t)last_round[s] & 1, abort_flag, st, 7, false);
                     wait_bar(&full[s], (uint32_t)last_round[s] & 1, abort_flag, st, 7, false);
+                }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -619,7 +635,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t k = 0; k < nkb; ++k, ++kc) {
                 const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
-                if (!wait_bar(&full[s], r & 1, abort_flag, st, 6)) { ok = false; break; }
+                if (!wait_bar(&lfull[s], r & 1, abort_flag, st, 6)) { ok = false; break; }
                 uint8_t* B = sm + s * g::STAGE_BYTES + g::A_BYTES;
                 const uint8_t* L = B + g::B_BYTES;
 #pragma unroll
@@ -628,10 +644,17 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     if (c < rows_used) {
                         const uint32_t pl = c / K, gg = c - pl * K;
                         const uint32_t rep = gg * 0x01010101u;
+                        // the label row's 64 bytes in four 16-byte loads (lanes of a
+                        // quarter-warp read at most two rows: no bank conflicts)
+                        uint32_t lw[16];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint4 v = *reinterpret_cast<const uint4*>(L + pl * g::BK + q * 16);
+                            lw[4 * q] = v.x; lw[4 * q + 1] = v.y; lw[4 * q + 2] = v.z; lw[4 * q + 3] = v.w;
+                        }
 #pragma unroll
                         for (uint32_t c8 = 0; c8 < 8; ++c8) {
-                            const uint2 lw = *reinterpret_cast<const uint2*>(L + pl * g::BK + c8 * 8);
-                            const uint32_t xs[2] = {lw.x ^ rep, lw.y ^ rep};
+                            const uint32_t xs[2] = {lw[2 * c8] ^ rep, lw[2 * c8 + 1] ^ rep};
                             uint32_t o[4];
 #pragma unroll
                             for (int hw = 0; hw < 2; ++hw) {

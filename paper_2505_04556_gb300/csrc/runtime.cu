@@ -10,15 +10,33 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <map>
+#include <tuple>
 #include <vector>
 
 using namespace pmn;
+
+namespace {
+// (log2 bucket of n, n_groups, log2 bucket of n_perms) -> tuned form
+using TuneKey = std::tuple<int, uint32_t, int>;
+// every argument of a permanova_sW call plus the form and the scratch arena
+using GraphKey = std::tuple<const void*, uint32_t, uint64_t, const void*, int, uint32_t, uint64_t,
+                            const void*, void*, void*, int, void*>;
+int log2_bucket(uint64_t x) {
+    int b = 0;
+    while ((1ull << b) < x && b < 63) ++b;
+    return b;
+}
+}  // namespace
 
 struct permanova_ctx {
     int device = 0;
     int sm_count = 0;
     size_t budget = 0;
     int forced_form = PERMANOVA_FORM_AUTO;
+    std::map<TuneKey, int> tuned;               // autotuner results
+    bool graphs = false;                        // replay captured launch sequences
+    std::map<GraphKey, cudaGraphExec_t> graph_cache;
     std::mutex mu;
     void* arena = nullptr;
     size_t arena_size = 0;
@@ -91,6 +109,8 @@ int label_bytes(int t) { return t == LABEL_U8 ? 1 : t == LABEL_U16 ? 2 : 4; }
 
 int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
     if (ctx->forced_form != PERMANOVA_FORM_AUTO) return ctx->forced_form;
+    auto it = ctx->tuned.find(TuneKey{log2_bucket(n), K, log2_bucket(P)});
+    if (it != ctx->tuned.end()) return it->second;
     // The tensor-core form costs 4K flops per pair and label row (two BF16
     // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
     // At the measured rates the GEMM form wins up to about K = 20.
@@ -158,6 +178,9 @@ int ensure_arena(permanova_ctx* ctx, size_t bytes) {
                     bytes, ctx->budget);
     size_t want = std::min(ctx->budget, std::max(bytes, ctx->arena_size + ctx->arena_size / 4));
     CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    // captured graphs point into the old arena
+    for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+    ctx->graph_cache.clear();
     if (ctx->arena) {
         cudaFree(ctx->arena);
         ctx->arena = nullptr;
@@ -333,6 +356,8 @@ void permanova_destroy(permanova_ctx* ctx) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         profile_clear(ctx);
+        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+        ctx->graph_cache.clear();
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->status) cudaFree(ctx->status);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
@@ -383,7 +408,95 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
     rc = ensure_arena(ctx, L.total);
     if (rc) return rc;
     SWProblem pr{mat, n, ld, groupings, label_type, K, P, nullptr, out};
-    return run_sW(ctx, L, pr, w, s);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool use_graph = ctx->graphs && !ctx->profiling && s != nullptr &&
+                           cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                           cap == cudaStreamCaptureStatusNone;
+    if (!use_graph) return run_sW(ctx, L, pr, w, s);
+    // replay the launch sequence of an identical earlier call, or capture it now
+    const GraphKey key{mat, n, ld, groupings, label_type, K, P, w, out, ctx->arena, L.form, nullptr};
+    auto it = ctx->graph_cache.find(key);
+    if (it == ctx->graph_cache.end()) {
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        rc = run_sW(ctx, L, pr, w, s);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        it = ctx->graph_cache.emplace(key, exec).first;
+    }
+    CK(cudaGraphLaunch(it->second, s), "cudaGraphLaunch");
+    return PERMANOVA_OK;
+}
+
+int permanova_set_graphs(permanova_ctx* ctx, int enable) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs) {
+        CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+        ctx->graph_cache.clear();
+    }
+    return PERMANOVA_OK;
+}
+
+int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                       const void* groupings, int label_type, uint32_t K, uint64_t P, const float* w,
+                       int* out_form, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    const double no_output = 0.0;   // the sample's results go to scratch
+    int rc = check_sW_args(mat, n, ld, groupings, label_type, K, P, w, &no_output);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // a sample of the caller's label rows sized to ~0.2 s of the fastest form
+    const double pairs = (double)n * (n - 1) / 2.0;
+    uint64_t Ps = (uint64_t)std::max(64.0, 4e11 / std::max(pairs, 1.0));
+    Ps = std::min<uint64_t>(Ps, std::min<uint64_t>(P, 4096));
+    const int forms[3] = {PERMANOVA_FORM_BRUTE, PERMANOVA_FORM_PERMBLOCK, PERMANOVA_FORM_GEMM};
+    double best_t = 1e300;
+    int best = PERMANOVA_FORM_BRUTE;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    for (int form : forms) {
+        // the brute force re-reads D per label row: skip it where it cannot win
+        if (form == PERMANOVA_FORM_BRUTE && Ps > 64 && pairs * Ps > 4e11) continue;
+        SWLayout L;
+        if (layout_for(ctx, form, n, ld, groupings, label_type, K, Ps, &L) != PERMANOVA_OK) continue;
+        const size_t out_off = align_up(L.total);
+        if (ensure_arena(ctx, out_off + (size_t)Ps * sizeof(double)) != PERMANOVA_OK) continue;
+        double* out = reinterpret_cast<double*>(static_cast<char*>(ctx->arena) + out_off);
+        SWProblem pr{mat, n, ld, groupings, label_type, K, Ps, nullptr, out};
+        float ms = 0.f;
+        bool ok = run_sW(ctx, L, pr, w, s) == PERMANOVA_OK;   // warm-up
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        ok = ok && run_sW(ctx, L, pr, w, s) == PERMANOVA_OK;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok && ms < best_t) {
+            best_t = ms;
+            best = form;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    rc = read_status(ctx, s);
+    if (rc) return rc;
+    ctx->tuned[TuneKey{log2_bucket(n), K, log2_bucket(P)}] = best;
+    if (out_form) *out_form = best;
+    return PERMANOVA_OK;
 }
 
 int permanova_profile_enable(permanova_ctx* ctx, int enable) {

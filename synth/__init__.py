@@ -112,6 +112,34 @@ def braycurtis_matrix(C) -> np.ndarray:
     return D
 
 
+def presence_features(labels, features: int = 1000, rate: float = 0.3, boost: float = 1.5,
+                      block: int = 50, seed: int = 0) -> np.ndarray:
+    """Sparse presence/absence profiles (a stand-in for microbiome feature
+    tables): feature f present with probability ``rate``, multiplied by
+    ``boost`` on the ``block`` features of the object's own group."""
+    labels = np.asarray(labels)
+    rng = np.random.default_rng(seed)
+    n = labels.shape[0]
+    p = np.full((n, features), rate)
+    cols = (block * labels[:, None] + np.arange(block)[None, :]) % features
+    p[np.arange(n)[:, None], cols] = min(1.0, rate * boost)
+    return rng.random((n, features)) < p
+
+
+def jaccard_matrix(B) -> np.ndarray:
+    """Jaccard distance 1 - |a & b| / |a | b| between presence rows, fp32 in
+    [0, 1] (0 for two empty rows); host, small n."""
+    B = np.asarray(B, dtype=np.float64)
+    inter = B @ B.T
+    cnt = B.sum(axis=1)
+    union = cnt[:, None] + cnt[None, :] - inter
+    with np.errstate(invalid="ignore", divide="ignore"):
+        D = np.where(union > 0, 1.0 - inter / union, 0.0)
+    D = D.astype(np.float32)
+    np.fill_diagonal(D, 0.0)
+    return D
+
+
 def integer_matrix(n: int, high: int, seed: int) -> np.ndarray:
     """Symmetric fp32 matrix with integer entries in [0, high], zero diagonal."""
     rng = np.random.default_rng(seed)
@@ -171,6 +199,10 @@ def recipe(name: str, n: int | None = None, P: int | None = None) -> dict:
         n = n or 50000
         sizes = largest_remainder_sizes(n, [25, 20, 15, 12, 10, 8, 6, 4])
         cfg = dict(dim=200, kind="braycurtis", K=8, P=P or 9999, label_type="u8", idx=3)
+    elif name == "jaccard-25k":      # the paper's benchmark shape: n=25,145, P=3,999
+        n = n or 25145               # distances in [0, 1] from sparse presence profiles
+        sizes = largest_remainder_sizes(n, [35, 25, 20, 12, 8])
+        cfg = dict(dim=1000, kind="jaccard", K=5, P=P or 3999, label_type="u8", idx=5)
     elif name == "euclid-100k":      # n=100,000, R^16, K=10 Dirichlet(2) sizes, P=99,999
         n = n or 100000
         sizes = dirichlet_sizes(n, 10, 2.0, SEED_POINTS + 4, min_size=2)
@@ -188,6 +220,8 @@ def recipe(name: str, n: int | None = None, P: int | None = None) -> dict:
 def recipe_points(cfg: dict) -> np.ndarray:
     if cfg["kind"] == "euclid":
         return gaussian_points(cfg["labels"], cfg["dim"], 0.3, cfg["seed_points"])
+    if cfg["kind"] == "jaccard":
+        return presence_features(cfg["labels"], features=cfg["dim"], seed=cfg["seed_points"])
     return dirichlet_compositions(cfg["labels"], features=cfg["dim"], seed=cfg["seed_points"])
 
 
@@ -195,6 +229,8 @@ def recipe_matrix_host(cfg: dict, X=None) -> np.ndarray:
     X = recipe_points(cfg) if X is None else X
     if cfg["kind"] == "euclid":
         return euclidean_matrix(X)
+    if cfg["kind"] == "jaccard":
+        return jaccard_matrix(X)
     return braycurtis_matrix(X)
 
 
@@ -212,6 +248,14 @@ def recipe_matrix_device(cfg: dict, X=None, device="cuda", chunk: int = 4096):
             r1 = min(n, r0 + chunk)
             blk = sq[r0:r1, None] + sq[None, :] - 2.0 * (Xd[r0:r1] @ Xd.T)
             D[r0:r1] = blk.clamp_min_(0.0).sqrt_().to(torch.float32)
+    elif cfg["kind"] == "jaccard":
+        cnt = Xd.sum(dim=1)
+        for r0 in range(0, n, chunk):
+            r1 = min(n, r0 + chunk)
+            inter = Xd[r0:r1] @ Xd.T
+            union = cnt[r0:r1, None] + cnt[None, :] - inter
+            blk = torch.where(union > 0, 1.0 - inter / union.clamp_min(1.0), torch.zeros_like(union))
+            D[r0:r1] = blk.to(torch.float32)
     else:
         tot = Xd.sum(dim=1)
         c = max(1, chunk // 16)

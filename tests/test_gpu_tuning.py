@@ -1,0 +1,74 @@
+"""Autotuner and CUDA-graph replay: the chosen plan and the replayed launch
+sequence give the same s_W as direct launches."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2505_04556_gb300 as pm  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pm.build()
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+def _case(n, K, P, seed):
+    rng = np.random.default_rng(seed)
+    D = synth.euclidean_matrix(rng.standard_normal((n, 6)))
+    sizes = synth.largest_remainder_sizes(n, rng.dirichlet(2 * np.ones(K)), min_size=1)
+    obs = synth.observed_labels(sizes, seed + 1)
+    rows = synth.shuffled_rows(obs, P, seed + 2)
+    return D, rows, synth.inv_sizes(obs, K)
+
+
+def test_autotune_then_auto_plan(ctx):
+    n, K, P = 900, 4, 300
+    D, rows, w = _case(n, K, P, 3)
+    Dd, lab, wd = (torch.from_numpy(D).cuda(), torch.from_numpy(rows.astype(np.uint8)).cuda(),
+                   torch.from_numpy(w).cuda())
+    form = pm.permanova_autotune(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd)
+    assert form in (pm.FORM_BRUTE, pm.FORM_PERMBLOCK, pm.FORM_GEMM)
+    assert pm.permanova_plan_form(ctx.handle, n, K, P) == form
+    out = ctx.sW(Dd, lab, K, wd)
+    pm.permanova_sync(ctx.handle)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5)
+
+
+def test_graph_replay_matches_direct_launches(ctx):
+    n, K, P = 700, 3, 200
+    D, rows, w = _case(n, K, P, 4)
+    Dd, wd = torch.from_numpy(D).cuda(), torch.from_numpy(w).cuda()
+    lab = torch.from_numpy(rows.astype(np.uint8)).cuda()
+    stream = torch.cuda.Stream()
+    direct = torch.empty(P, dtype=torch.float64, device="cuda")
+    pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, direct, stream)
+    pm.permanova_sync(ctx.handle, stream)
+    pm.permanova_set_graphs(ctx.handle, True)
+    try:
+        out = torch.empty(P, dtype=torch.float64, device="cuda")
+        for _ in range(3):   # capture once, then replay
+            out.fill_(float("nan"))
+            pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, out, stream)
+            pm.permanova_sync(ctx.handle, stream)
+            assert torch.equal(out, direct)
+        # replays read the buffers at run time: new labels in the same buffer
+        rows2 = synth.shuffled_rows(rows[0], P, 99)
+        with torch.cuda.stream(stream):
+            lab.copy_(torch.from_numpy(rows2.astype(np.uint8)))
+        pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, out, stream)
+        pm.permanova_sync(ctx.handle, stream)
+        ref2 = oracle.sW_alg1(D, rows2, K, w.astype(np.float64))
+        np.testing.assert_allclose(out.cpu().numpy(), ref2, rtol=1e-5)
+    finally:
+        pm.permanova_set_graphs(ctx.handle, False)

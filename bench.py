@@ -38,8 +38,10 @@ WORKLOADS = {
     "euclid-100k": dict(batch=8192),
     "braycurtis-50k": dict(batch=8192),
     "euclid-20k": dict(batch=4000),
+    "jaccard-25k": dict(batch=4000),
     "euclid-1k": dict(batch=1000),
 }
+L2_BYTES = 129 << 20
 
 
 def peaks() -> dict:
@@ -140,9 +142,8 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
     K = cfg["K"]
     w = cfg["w"].astype(np.float64)
 
-    ns = min(X.shape[0], 16384)
-    D = synth.euclidean_matrix(X[:ns]) if cfg["kind"] == "euclid" else \
-        synth.braycurtis_matrix(X[:ns])
+    ns = min(X.shape[0], 4096 if cfg["kind"] == "braycurtis" else 16384)
+    D = synth.recipe_matrix_host(cfg, X[:ns])
     pairs_s = ns * (ns - 1) / 2
 
     def run(R: int) -> float:
@@ -387,25 +388,36 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    # D larger than L2 needs no flush; a small D is flushed from L2 between
+    # steps (a write of 2 x L2), and only the steps themselves are timed
+    flush = None
+    if n * n * 4 < 2 * L2_BYTES:
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     sampler = ClockSampler(gpu_query_id(torch, dev))
     pm.permanova_profile_enable(ctx.handle, True)
     torch.cuda.synchronize(dev)
     barrier()
     sampler.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps if flush is not None else 1)]
+    ev[0][0].record(stream)
     rows_done = 0
     for k in range(args.steps):
+        if flush is not None and k > 0:
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            ev[k][0].record(stream)
         rows_done += step(args.warmup + k)
-    t_end.record(stream)
+        if flush is not None:
+            ev[k][1].record(stream)
+    ev[-1][1].record(stream)
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
     prof = pm.permanova_profile_read(ctx.handle)
     pm.permanova_profile_enable(ctx.handle, False)
     pm.permanova_sync(ctx.handle, stream)
-    ms, rows_total = combine_ranks(t_start.elapsed_time(t_end), float(rows_done))
+    ms, rows_total = combine_ranks(sum(a.elapsed_time(b) for a, b in ev), float(rows_done))
     value = pairs * rows_total / (ms / 1e3)
 
     # ---- dominant kernel roofline ----
@@ -458,9 +470,14 @@ def main():
                 "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "n": n, "K": K, "P_total": P,
                            "batch": B, "label_type": "u8", "form": form,
-                           "matrix": "Gaussian points in R^16 (group shift 0.3 sd), Euclidean fp32"
-                           if cfg["kind"] == "euclid" else "Dirichlet(0.5) x 200, Bray-Curtis fp32",
-                           "l2": f"inputs larger than L2 (D = {n * n * 4 / 1e9:.1f} GB)",
+                           "matrix": {"euclid": f"Gaussian points in R^{cfg['dim']} (group shift "
+                                                f"0.3 sd), Euclidean fp32",
+                                      "braycurtis": "Dirichlet(0.5) x 200, Bray-Curtis fp32",
+                                      "jaccard": "presence profiles (1,000 features), Jaccard fp32"
+                                      }[cfg["kind"]],
+                           "l2": (f"inputs larger than L2 (D = {n * n * 4 / 1e9:.1f} GB)"
+                                  if flush is None else
+                                  "L2 flushed between steps (2 x L2 write, untimed)"),
                            "parallelism": f"replicas x{world} (label rows split)"},
                 "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(prof["kernel_launches"]),

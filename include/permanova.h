@@ -125,6 +125,15 @@ int permanova_autotune(permanova_ctx *ctx, const float *mat, uint32_t n_dims, ui
  * captured, and profiled calls, launch directly. */
 int permanova_set_graphs(permanova_ctx *ctx, int enable);
 
+/* Failure-detection self-test (not a paper operation): launches, on
+ * `stream`, a kernel whose one thread waits on a device barrier that nothing
+ * ever completes, using the same bounded wait as the tensor-core kernel.
+ * After limit_us microseconds (1 .. 10,000,000) the wait gives up, records
+ * the timeout in the context's device error word and the kernel returns; the
+ * next permanova_sync reports PERMANOVA_ETIMEOUT and the context stays
+ * usable.  Asynchronous; EINVAL for a limit out of range. */
+int permanova_selftest_wait(permanova_ctx *ctx, uint32_t limit_us, void *stream);
+
 /* Bytes of context scratch a permanova_sW call of these sizes needs under
  * `form` (AUTO = the planner's form).  0 on invalid sizes. */
 size_t permanova_scratch_bytes(permanova_ctx *ctx, int form, uint32_t n_dims, uint32_t n_groups,

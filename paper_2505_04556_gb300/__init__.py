@@ -105,6 +105,8 @@ def load(path: str | None = None):
         lib.permanova_autotune.argtypes = [vp, vp, u32, u64, vp, i32, u32, u64, vp,
                                            ctypes.POINTER(i32), vp]
         lib.permanova_autotune.restype = i32
+        lib.permanova_selftest_wait.argtypes = [vp, u32, vp]
+        lib.permanova_selftest_wait.restype = i32
         lib.permanova_set_graphs.argtypes = [vp, i32]
         lib.permanova_set_graphs.restype = i32
         lib.permanova_sW_noalloc.argtypes = [vp, u32, u64, vp, i32, u32, u64, vp, vp, vp]
@@ -220,6 +222,10 @@ def permanova_autotune(ctx, mat, n_dims: int, ld: int, groupings, label_type: in
                                    _ptr(inv_group_sizes), ctypes.byref(form), _stream(stream))
     _check(ctx, rc)
     return form.value
+
+
+def permanova_selftest_wait(ctx, limit_us: int, stream=None) -> None:
+    _check(ctx, load().permanova_selftest_wait(ctx, int(limit_us), _stream(stream)))
 
 
 def permanova_set_graphs(ctx, enable: bool = True) -> None:

@@ -124,6 +124,9 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s);
 
+// a bounded wait on an mbarrier that never completes (failure-detection self-test)
+cudaError_t launch_wait_selftest(DevStatus* st, long long limit_cycles, cudaStream_t s);
+
 // permutation test helpers
 cudaError_t launch_permutations(const int32_t* grouping, uint32_t n, uint64_t n_perms,
                                 uint64_t seed, void* out, int label_type, cudaStream_t s);

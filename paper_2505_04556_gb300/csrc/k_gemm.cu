@@ -366,18 +366,39 @@ struct GemmArgs {
 // Bounded wait.  With `obey_abort` the wait also gives up once another role
 // has aborted.  Returns true when the phase completed.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         DevStatus* st, unsigned where, bool obey_abort = true) {
+                                         DevStatus* st, unsigned where, bool obey_abort = true,
+                                         long long limit = g::WAIT_LIMIT) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_test(bar, parity)) return true;
         if (obey_abort && *abort_flag) return false;
-        if (clock64() - t0 > g::WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             raise_status(st, DEV_TIMEOUT, where, 0ull);
             return false;
         }
     }
+}
+
+// Self-test of the bounded wait the kernel above relies on: one thread waits
+// on an mbarrier that nothing arrives on; after `limit` cycles the wait gives
+// up, records DEV_TIMEOUT and the kernel returns normally.
+__global__ void k_wait_selftest(DevStatus* st, long long limit) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) wait_bar(&bar, 0, &abort_flag, st, 99, false, limit);
+}
+
+cudaError_t launch_wait_selftest(DevStatus* st, long long limit_cycles, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(st, limit_cycles);
+    return launched(1);
 }
 
 __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {

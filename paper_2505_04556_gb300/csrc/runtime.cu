@@ -436,6 +436,18 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
     return PERMANOVA_OK;
 }
 
+int permanova_selftest_wait(permanova_ctx* ctx, uint32_t limit_us, void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    if (limit_us == 0 || limit_us > 10000000u) return fail(PERMANOVA_EINVAL, "limit_us out of range");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+    const long long cycles = (long long)limit_us * (khz > 0 ? khz : 2000000) / 1000;
+    CK(launch_wait_selftest(ctx->status, cycles, static_cast<cudaStream_t>(stream)), "wait self-test");
+    return PERMANOVA_OK;
+}
+
 int permanova_set_graphs(permanova_ctx* ctx, int enable) {
     if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);

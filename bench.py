@@ -459,7 +459,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rows_h = lab[:64].cpu().numpy() if not args.no_e2e else labh[:64].numpy()
+        rows_h = lab[:64].cpu().numpy()
         cpu = oracle_rate(cfg, X, rows_h, 15.0)
 
     if rank == 0:

@@ -255,6 +255,23 @@ int permanova_test(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64
                    const int32_t *grouping, uint32_t n_groups, uint64_t n_perms, uint64_t seed,
                    permanova_result *out_host, double *out_sW, void *stream);
 
+/* n_tests permutation tests on one matrix in one pass (the batching a server
+ * applies to requests on the same matrix with the same n_groups and n_perms).
+ *   groupings  DEVICE, n_tests rows of n_dims int32 observed labels (row t =
+ *              test t), each in [0, n_groups) with every group non-empty.
+ *   seeds      HOST, n_tests permutation seeds.
+ *   out_host   HOST, n_tests results.
+ *   out_sW     optional DEVICE buffer of n_tests x (n_perms + 1) doubles.
+ * All tests' label rows go through one s_W launch, each test weighted by its
+ * own 1/n_g; the kernel form is the one a single test of these sizes gets,
+ * so every result equals the corresponding permanova_test call bit for bit.
+ * Synchronises `stream`; errors as permanova_test (the message names the
+ * test). */
+int permanova_test_batch(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                         const int32_t *groupings, uint32_t n_tests, uint32_t n_groups,
+                         uint64_t n_perms, const uint64_t *seeds, permanova_result *out_host,
+                         double *out_sW, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,9 @@ def load(path: str | None = None):
         lib.permanova_autotune.argtypes = [vp, vp, u32, u64, vp, i32, u32, u64, vp,
                                            ctypes.POINTER(i32), vp]
         lib.permanova_autotune.restype = i32
+        lib.permanova_test_batch.argtypes = [vp, vp, u32, u64, vp, u32, u32, u64, vp,
+                                             ctypes.POINTER(permanova_result), vp, vp]
+        lib.permanova_test_batch.restype = i32
         lib.permanova_selftest_wait.argtypes = [vp, u32, vp]
         lib.permanova_selftest_wait.restype = i32
         lib.permanova_set_graphs.argtypes = [vp, i32]
@@ -222,6 +225,18 @@ def permanova_autotune(ctx, mat, n_dims: int, ld: int, groupings, label_type: in
                                    _ptr(inv_group_sizes), ctypes.byref(form), _stream(stream))
     _check(ctx, rc)
     return form.value
+
+
+def permanova_test_batch(ctx, mat, n_dims: int, ld: int, groupings, n_tests: int, n_groups: int,
+                         n_perms: int, seeds, out_sW=None, stream=None) -> list:
+    res = (permanova_result * n_tests)()
+    sd = (ctypes.c_uint64 * n_tests)(*[int(x) & (2**64 - 1) for x in seeds])
+    rc = load().permanova_test_batch(ctx, _ptr(mat), int(n_dims), int(ld), _ptr(groupings),
+                                     int(n_tests), int(n_groups), int(n_perms),
+                                     ctypes.cast(sd, ctypes.c_void_p), res, _ptr(out_sW),
+                                     _stream(stream))
+    _check(ctx, rc)
+    return [r.as_dict() for r in res]
 
 
 def permanova_selftest_wait(ctx, limit_us: int, stream=None) -> None:

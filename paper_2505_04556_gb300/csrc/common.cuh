@@ -59,7 +59,16 @@ struct SWProblem {
     uint64_t P;
     const double* w;       // inv_group_sizes widened to FP64 (device)
     double* out;
+    // Weight sets: 0 = one set of K weights for every label row; otherwise
+    // label row p uses w[(p / w_set_rows) * K + g] (several tests in one pass).
+    uint64_t w_set_rows;
 };
+
+// Weight of group g for label row p.
+__host__ __device__ __forceinline__ const double* weight_row(const double* w, uint64_t p,
+                                                             uint64_t w_set_rows, uint32_t K) {
+    return w_set_rows ? w + (p / w_set_rows) * K : w;
+}
 
 // inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
 cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t s);
@@ -140,5 +149,12 @@ struct TestScalars {
 };
 cudaError_t launch_finalize(const double* sW, uint64_t n_perms, const double* sT_sum, uint32_t n,
                             uint32_t K, TestScalars* out, cudaStream_t s);
+// n_tests tests in one pass: sW and out hold n_tests segments / results
+cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
+                                  const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,
+                                  cudaStream_t s);
+cudaError_t launch_permutations_batch(const int32_t* groupings, uint32_t n, uint32_t n_tests,
+                                      uint64_t n_perms, const uint64_t* seeds, void* out,
+                                      int label_type, cudaStream_t s);
 
 }  // namespace pmn

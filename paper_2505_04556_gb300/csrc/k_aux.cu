@@ -265,10 +265,13 @@ cudaError_t launch_permutations(const int32_t* grouping, uint32_t n, uint64_t n_
 // #{p >= 1 : s_W[p] <= s_W[0]}.  For fixed s_T, n and K, pseudo-F decreases
 // strictly in s_W, so F_p >= F_obs is the same event as s_W[p] <= s_W_obs.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(const double* __restrict__ sW, uint64_t n_perms,
+// One block per test; test t's label rows are sW[t*(n_perms+1) ...].
+__global__ void k_finalize(const double* __restrict__ sW_all, uint64_t n_perms,
                            const double* __restrict__ sT_sum, uint32_t n, uint32_t K,
-                           TestScalars* out) {
+                           TestScalars* out_all) {
     __shared__ unsigned long long cnt[32];
+    const double* sW = sW_all + (uint64_t)blockIdx.x * (n_perms + 1);
+    TestScalars* out = out_all + blockIdx.x;
     const double obs = sW[0];
     unsigned long long c = 0;
     for (uint64_t p = 1 + threadIdx.x; p <= n_perms; p += blockDim.x) c += (sW[p] <= obs) ? 1ull : 0ull;
@@ -293,6 +296,73 @@ cudaError_t launch_finalize(const double* sW, uint64_t n_perms, const double* sT
                             uint32_t K, TestScalars* out, cudaStream_t s) {
     k_finalize<<<1, 1024, 0, s>>>(sW, n_perms, sT_sum, n, K, out);
     return launched(1);
+}
+
+cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
+                                  const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,
+                                  cudaStream_t s) {
+    k_finalize<<<n_tests, 1024, 0, s>>>(sW, n_perms, sT_sum, n, K, out);
+    return launched(1);
+}
+
+// ---------------------------------------------------------------------------
+// Several tests at once: test t has its own observed grouping (row t of
+// `groupings`) and seed; its label rows are t*(n_perms+1) .. (t+1)*(n_perms+1)-1,
+// the first being the observed grouping.  Each shuffle is the same as a
+// single test's with that seed.
+// ---------------------------------------------------------------------------
+template <typename L>
+__global__ void k_copy_groupings(const int32_t* __restrict__ g, uint32_t n, uint32_t n_tests,
+                                 uint64_t rows_per_test, L* __restrict__ out) {
+    const uint64_t total = (uint64_t)n * rows_per_test * n_tests;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+        const uint64_t row = k / n, t = row / rows_per_test;
+        out[k] = (L)g[t * n + (k - row * n)];
+    }
+}
+
+template <typename L>
+__global__ void k_fisher_yates_batch(uint32_t n, uint64_t n_perms, uint32_t n_tests,
+                                     const uint64_t* __restrict__ seeds, L* __restrict__ out) {
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_perms * n_tests) return;
+    const uint64_t t = idx / n_perms;
+    const uint32_t p = (uint32_t)(idx - t * n_perms + 1);
+    L* a = out + (t * (n_perms + 1) + p) * n;
+    Philox4x32 rng;
+    const uint64_t seed = seeds[t];
+    rng.k0 = (uint32_t)seed;
+    rng.k1 = (uint32_t)(seed >> 32);
+    rng.c0 = 0u;
+    rng.c2 = p;
+    rng.used = 4;
+    for (uint32_t i = n - 1; i >= 1; --i) {
+        const uint32_t j = rng.bounded(i + 1);
+        const L ai = a[i];
+        a[i] = a[j];
+        a[j] = ai;
+    }
+}
+
+template <typename L>
+static void perms_batch_t(const int32_t* g, uint32_t n, uint32_t n_tests, uint64_t n_perms,
+                          const uint64_t* seeds, L* out, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((n_perms * n_tests + 127) / 128);
+    k_copy_groupings<L><<<152 * 8, 256, 0, s>>>(g, n, n_tests, n_perms + 1, out);
+    k_fisher_yates_batch<L><<<blocks, 128, 0, s>>>(n, n_perms, n_tests, seeds, out);
+}
+
+cudaError_t launch_permutations_batch(const int32_t* groupings, uint32_t n, uint32_t n_tests,
+                                      uint64_t n_perms, const uint64_t* seeds, void* out,
+                                      int label_type, cudaStream_t s) {
+    if (label_type == LABEL_U8)
+        perms_batch_t<uint8_t>(groupings, n, n_tests, n_perms, seeds, (uint8_t*)out, s);
+    else if (label_type == LABEL_U16)
+        perms_batch_t<uint16_t>(groupings, n, n_tests, n_perms, seeds, (uint16_t*)out, s);
+    else
+        perms_batch_t<int32_t>(groupings, n, n_tests, n_perms, seeds, (int32_t*)out, s);
+    return launched(2);
 }
 
 }  // namespace pmn

@@ -62,8 +62,7 @@ constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES + LAB_BYTES;   // 68 KB
 constexpr uint32_t OFF_LABROWS = NST * STAGE_BYTES;
 constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][NMAX] float
 constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * NMAX * 4;        // [NMAX] double
-constexpr uint32_t OFF_W = OFF_ACC64 + NMAX * 8;                  // [256] double
-constexpr uint32_t OFF_BAR = OFF_W + 256 * 8;
+constexpr uint32_t OFF_BAR = OFF_ACC64 + NMAX * 8;
 constexpr uint32_t N_BARS = 4 * NST + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
@@ -351,6 +350,7 @@ struct GemmArgs {
     const uint8_t* tiles;      // prepared A tiles
     const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
     const double* w;
+    uint64_t w_set_rows;       // label rows per weight set (0: one set)
     double* partials;          // n_bands x P
     DevStatus* st;
     uint64_t P;
@@ -419,7 +419,6 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
     float* red = reinterpret_cast<float*>(sm + g::OFF_RED);      // [2][4][NMAX]
     double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);
-    double* wtab = reinterpret_cast<double*>(sm + g::OFF_W);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevStatus* st = a.st;
@@ -440,7 +439,6 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         *abort_flag = (st->code != DEV_OK) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (uint32_t k = threadIdx.x; k < 256; k += blockDim.x) wtab[k] = k < a.K ? __ldg(a.w + k) : 0.0;
     // B rows beyond ppt*K stay zero in every stage
     for (uint32_t e = threadIdx.x; e < g::NST * (g::B_BYTES / 16); e += blockDim.x) {
         const uint32_t s = e / (g::B_BYTES / 16), o = e % (g::B_BYTES / 16);
@@ -548,8 +546,6 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         const uint32_t used = a.ppt * K;           // accumulator columns that carry a (p, g)
         // the two accumulator columns this thread finalises, and their group weights
         const uint32_t cA = et, cB = et + 128;
-        const double wA = cA < used ? wtab[cA % K] : 0.0;
-        const double wB = cB < used ? wtab[cB % K] : 0.0;
         double accA = 0.0, accB = 0.0;
         uint64_t cc = 0;
         uint32_t epi_phase = 0;
@@ -558,6 +554,11 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint32_t I = (uint32_t)(u / a.n_ptiles);
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
+            // the group weights of this thread's two columns (label row p0 + c/K, group c%K)
+            const double wA = (cA < used && cA / K < nlab)
+                                  ? __ldg(weight_row(a.w, p0 + cA / K, a.w_set_rows, K) + cA % K) : 0.0;
+            const double wB = (cB < used && cB / K < nlab)
+                                  ? __ldg(weight_row(a.w, p0 + cB / K, a.w_set_rows, K) + cB % K) : 0.0;
             // the band's row labels for the tile's label rows: k-blocks 2I and 2I+1 of
             // the tile's label blocks, loaded cooperatively (16 bytes per thread-step)
             {
@@ -713,6 +714,7 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     a.tiles = (const uint8_t*)scratch;
     a.labels = (const uint8_t*)pr.labels;
     a.w = pr.w;
+    a.w_set_rows = pr.w_set_rows;
     a.partials = partials;
     a.st = st;
     a.P = pr.P;

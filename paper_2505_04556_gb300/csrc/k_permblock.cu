@@ -79,7 +79,8 @@ __device__ __forceinline__ void load_col_codes<uint16_t>(const uint16_t* __restr
 template <typename L, bool VEC>
 __global__ void __launch_bounds__(PB_P, 4)
 k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __restrict__ labels,
-               uint64_t lstride, uint64_t P, const double* __restrict__ w, uint32_t K,
+               uint64_t lstride, uint64_t P, const double* __restrict__ w_all, uint64_t w_set_rows,
+               uint32_t K,
                uint32_t n_pblocks, double* __restrict__ partials, const DevStatus* __restrict__ st) {
     __shared__ __align__(16) float d2[PB_T][PB_T];
     const uint32_t band = blockIdx.x / n_pblocks;
@@ -92,6 +93,7 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     }
     // inactive threads of the last block mirror the last row so loads stay in bounds
     const L* g = labels + (active ? p : P - 1) * lstride;
+    const double* w = weight_row(w_all, active ? p : P - 1, w_set_rows, K);
     const uint32_t r0 = band * PB_T;
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     double total = 0.0;
@@ -167,11 +169,11 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     if (vec)
         k_sw_permblock<L, true><<<(unsigned)blocks, PB_P, 0, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.K,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
             (uint32_t)n_pblocks, partials, st);
     else
         k_sw_permblock<L, false><<<(unsigned)blocks, PB_P, 0, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.K,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
             (uint32_t)n_pblocks, partials, st);
     return launched(1);
 }

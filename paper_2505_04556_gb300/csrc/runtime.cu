@@ -243,13 +243,18 @@ void profile_clear(permanova_ctx* ctx) {
 
 // The s_W path on device buffers; the arena is already large enough.
 // `wf` (device fp32 inv_group_sizes) is widened into the layout's FP64 slot;
-// with wf == NULL the slot already holds the FP64 weights.
+// with wf == NULL, pr.w (FP64, possibly several weight sets) is used, or the
+// layout's slot when pr.w is NULL.
 int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s) {
     char* base = static_cast<char*>(ctx->arena);
     double* partials = reinterpret_cast<double*>(base + L.part_off);
     double* wd = reinterpret_cast<double*>(base + L.w_off);
-    if (wf) CK(launch_widen(wf, pr.K, wd, s), "widen weights");
-    pr.w = wd;
+    if (wf) {
+        CK(launch_widen(wf, pr.K, wd, s), "widen weights");
+        pr.w = wd;
+    } else if (!pr.w) {
+        pr.w = wd;
+    }
     SWProblem q = pr;
     if (L.form == PERMANOVA_FORM_BRUTE) {
         CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K, ctx->status, s),
@@ -610,8 +615,16 @@ int permanova_permutations(permanova_ctx* ctx, const int32_t* grouping, uint32_t
 int permanova_test(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
                    const int32_t* grouping, uint32_t K, uint64_t P, uint64_t seed,
                    permanova_result* out_host, double* out_sW, void* stream) {
+    return permanova_test_batch(ctx, mat, n, ld, grouping, 1, K, P, &seed, out_host, out_sW, stream);
+}
+
+int permanova_test_batch(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                         const int32_t* groupings, uint32_t T, uint32_t K, uint64_t P,
+                         const uint64_t* seeds, permanova_result* out_host, double* out_sW,
+                         void* stream) {
     if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
-    if (!mat || !grouping || !out_host) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (!mat || !groupings || !out_host || !seeds) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (T == 0) return fail(PERMANOVA_EINVAL, "n_tests must be >= 1");
     if (K < 2) return fail(PERMANOVA_EINVAL, "the test needs n_groups >= 2 (got %u)", K);
     if (n <= K) return fail(PERMANOVA_EINVAL, "the test needs n_dims > n_groups (pseudo-F undefined)");
     if (ld < n) return fail(PERMANOVA_EINVAL, "ld < n_dims");
@@ -620,27 +633,34 @@ int permanova_test(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // group sizes -> inv_group_sizes (host), observed labels checked here
-    std::vector<int32_t> hg(n);
-    CK(cudaMemcpyAsync(hg.data(), grouping, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-       "copy grouping");
+    // group sizes -> inv_group_sizes 1/n_g in FP64 (host), observed labels checked here
+    std::vector<int32_t> hg((size_t)n * T);
+    CK(cudaMemcpyAsync(hg.data(), groupings, hg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+       "copy groupings");
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    std::vector<uint64_t> sizes(K, 0);
-    for (uint32_t i = 0; i < n; ++i) {
-        if (hg[i] < 0 || (uint32_t)hg[i] >= K)
-            return fail(PERMANOVA_EINVAL, "grouping[%u] = %d outside [0, %u)", i, hg[i], K);
-        sizes[hg[i]] += 1;
-    }
-    std::vector<double> hw(K);   // inv_group_sizes 1/n_g, kept in FP64
-    for (uint32_t k = 0; k < K; ++k) {
-        if (sizes[k] == 0) return fail(PERMANOVA_EINVAL, "group %u is empty", k);
-        hw[k] = 1.0 / (double)sizes[k];
+    std::vector<double> hw((size_t)K * T);
+    std::vector<uint64_t> sizes(K);
+    for (uint32_t t = 0; t < T; ++t) {
+        std::fill(sizes.begin(), sizes.end(), 0);
+        for (uint32_t i = 0; i < n; ++i) {
+            const int32_t lab = hg[(size_t)t * n + i];
+            if (lab < 0 || (uint32_t)lab >= K)
+                return fail(PERMANOVA_EINVAL, "test %u: grouping[%u] = %d outside [0, %u)", t, i, lab, K);
+            sizes[lab] += 1;
+        }
+        for (uint32_t k = 0; k < K; ++k) {
+            if (sizes[k] == 0) return fail(PERMANOVA_EINVAL, "test %u: group %u is empty", t, k);
+            hw[(size_t)t * K + k] = 1.0 / (double)sizes[k];
+        }
     }
 
-    const uint64_t rows = P + 1;
+    // every test's label rows in one pass; the form is the one a single test
+    // would get, so a batched test gives the same numbers as a lone one
+    const uint64_t per = P + 1, rows = per * T;
     const int lt = K <= 256 ? LABEL_U8 : K <= 65536 ? LABEL_U16 : LABEL_I32;
+    const int form = plan_form(ctx, n, K, per);
     SWLayout L;
-    int rc = layout_for(ctx, plan_form(ctx, n, K, rows), n, ld, nullptr, lt, K, rows, &L);
+    int rc = layout_for(ctx, form, n, ld, nullptr, lt, K, rows, &L);
     if (rc) return rc;
     size_t off = L.total;
     const size_t lab_off = off;
@@ -650,35 +670,48 @@ int permanova_test(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld
     const uint32_t chunks = brute_chunks(n, ctx->sm_count);
     const size_t st_off = off;
     off = align_up(off + (size_t)(chunks + 1) * sizeof(double));
+    const size_t w_off = off;
+    off = align_up(off + hw.size() * sizeof(double));
+    const size_t seed_off = off;
+    off = align_up(off + (size_t)T * sizeof(uint64_t));
+    const size_t res_off = off;
+    off = align_up(off + (size_t)T * sizeof(TestScalars));
     rc = ensure_arena(ctx, off);
     if (rc) return rc;
     char* base = static_cast<char*>(ctx->arena);
     void* labels = base + lab_off;
     double* sW = out_sW ? out_sW : reinterpret_cast<double*>(base + sw_off);
     double* st_part = reinterpret_cast<double*>(base + st_off);
+    double* wsets = reinterpret_cast<double*>(base + w_off);
+    uint64_t* dseeds = reinterpret_cast<uint64_t*>(base + seed_off);
+    TestScalars* dres = reinterpret_cast<TestScalars*>(base + res_off);
 
-    CK(launch_permutations(grouping, n, P, seed, labels, lt, s), "permutation kernels");
-    rc = layout_for(ctx, L.form, n, ld, labels, lt, K, rows, &L);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(base + L.w_off, hw.data(), (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s),
+    CK(cudaMemcpyAsync(dseeds, seeds, (size_t)T * sizeof(uint64_t), cudaMemcpyHostToDevice, s), "copy seeds");
+    CK(cudaMemcpyAsync(wsets, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice, s),
        "copy weights");
-    SWProblem pr{mat, n, ld, labels, lt, K, rows, nullptr, sW};
+    CK(launch_permutations_batch(groupings, n, T, P, dseeds, labels, lt, s), "permutation kernels");
+    rc = layout_for(ctx, form, n, ld, labels, lt, K, rows, &L);
+    if (rc) return rc;
+    SWProblem pr{mat, n, ld, labels, lt, K, rows, wsets, sW};
+    pr.w_set_rows = per;
     rc = run_sW(ctx, L, pr, nullptr, s);
     if (rc) return rc;
     CK(launch_sumsq_triangle(mat, n, ld, chunks, st_part, s), "sum of squares kernel");
     CK(launch_reduce_rows(st_part, chunks, 1, st_part + chunks, s), "reduce s_T");
-    CK(launch_finalize(sW, P, st_part + chunks, n, K, ctx->scalars, s), "finalize kernel");
-    CK(cudaMemcpyAsync(ctx->scalars_host, ctx->scalars, sizeof(TestScalars), cudaMemcpyDeviceToHost, s),
-       "copy result");
+    CK(launch_finalize_batch(sW, T, P, st_part + chunks, n, K, dres, s), "finalize kernel");
+    std::vector<TestScalars> hres(T);
+    CK(cudaMemcpyAsync(hres.data(), dres, (size_t)T * sizeof(TestScalars), cudaMemcpyDeviceToHost, s),
+       "copy results");
     rc = read_status(ctx, s);
     if (rc) return rc;
-    const TestScalars& t = *ctx->scalars_host;
-    out_host->s_T = t.s_T;
-    out_host->s_W_obs = t.s_W_obs;
-    out_host->F_obs = t.F_obs;
-    out_host->p_value = t.p_value;
-    out_host->n_ge = t.n_ge;
-    out_host->n_perms = t.n_perms;
+    for (uint32_t t = 0; t < T; ++t) {
+        out_host[t].s_T = hres[t].s_T;
+        out_host[t].s_W_obs = hres[t].s_W_obs;
+        out_host[t].F_obs = hres[t].F_obs;
+        out_host[t].p_value = hres[t].p_value;
+        out_host[t].n_ge = hres[t].n_ge;
+        out_host[t].n_perms = hres[t].n_perms;
+    }
     return PERMANOVA_OK;
 }
 

@@ -5,13 +5,18 @@ arrive at any time.  Distance matrices stay resident in HBM.  A request is
 admitted as soon as an execution slot is free and its scratch fits the HBM
 budget left by the requests already running; requests that arrive while
 others run are admitted as slots and memory free up, so the GPU always holds
-the work of several tests at once.  Each slot owns a permanova context (its
-own scratch arena) and a CUDA stream, and runs ``permanova_test`` through
-the C ABI; slots run concurrently, their kernels overlap on the device.
+the work of several tests at once.  When a slot frees up, the waiting
+requests on the same matrix with the same number of groups and permutations
+are batched with the oldest one into a single ``permanova_test_batch`` call:
+one permutation launch, one s_W launch over all their label rows (each test
+with its own weights), one finalize launch.  Each slot owns a permanova
+context (its own scratch arena) and a CUDA stream; slots run concurrently and
+their kernels overlap on the device.
 
 Results do not depend on the mix: every test's kernels are deterministic
-(fixed-order reductions), so a test gives bit-identical s_W, F and p alone
-and among other traffic.
+(fixed-order reductions, per-row results independent of the other rows in a
+launch, the kernel form chosen by a single test's sizes), so a test gives
+bit-identical s_W, F and p alone, batched, and among other traffic.
 
 Latency is measured from arrival (submit) to completion; the server reports
 tests/s and p50/p99 latency.
@@ -23,6 +28,8 @@ import queue
 import threading
 import time
 from dataclasses import dataclass, field
+
+import numpy as np
 
 import paper_2505_04556_gb300 as pm
 
@@ -39,6 +46,7 @@ class Request:
     t_done: float = 0.0
     result: dict | None = None
     error: str | None = None
+    batch_size: int = 1       # tests that shared this request's launch
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -50,9 +58,10 @@ class Server:
     """``matrices``: dict id -> square fp32 CUDA tensor (resident)."""
 
     def __init__(self, matrices: dict, n_slots: int = 4, hbm_budget_bytes: int = 0,
-                 device: int = 0):
+                 device: int = 0, max_batch: int = 16):
         import torch
         self.torch = torch
+        self.max_batch = max_batch
         self.device = device
         self.matrices = matrices
         free, _ = torch.cuda.mem_get_info(device)
@@ -96,37 +105,63 @@ class Server:
 
     def _dispatch(self):
         while True:
+            slot = self.free_slots.get()          # blocks until a slot frees up
             with self.cv:
                 while self.running and (not self.pending or
                                         self.pending[0]._need + self.in_use > self.budget):
                     self.cv.wait(timeout=0.05)
                 if not self.running:
+                    self.free_slots.put(slot)
                     return
-                req = self.pending.popleft()
-                self.in_use += req._need
-            slot = self.free_slots.get()          # blocks until a slot frees up
-            threading.Thread(target=self._run, args=(slot, req), daemon=True).start()
+                head = self.pending.popleft()
+                self.in_use += head._need
+                batch = [head]
+                # requests already waiting that can share the launch: same matrix,
+                # same number of groups and permutations (one s_W pass for all)
+                key = (head.matrix_id, head.n_groups, head.n_perms)
+                for r in list(self.pending):
+                    if len(batch) >= self.max_batch:
+                        break
+                    if ((r.matrix_id, r.n_groups, r.n_perms) == key
+                            and self.in_use + r._need <= self.budget):
+                        self.pending.remove(r)
+                        self.in_use += r._need
+                        batch.append(r)
+            threading.Thread(target=self._run, args=(slot, batch), daemon=True).start()
 
-    def _run(self, slot: int, req: Request):
+    def _run(self, slot: int, batch: list[Request]):
         torch = self.torch
         ctx, stream = self.slots[slot]
+        t0 = time.perf_counter()
+        for r in batch:
+            r.t_start = t0
         try:
-            req.t_start = time.perf_counter()
-            D = self.matrices[req.matrix_id]
+            head = batch[0]
+            D = self.matrices[head.matrix_id]
             with torch.cuda.stream(stream):
-                g = torch.from_numpy(req.grouping).to(device=D.device, non_blocking=False)
-                req.result = ctx.test(D, g, req.n_groups, req.n_perms, req.seed,
-                                      stream=stream.cuda_stream)
+                g = torch.from_numpy(np.stack([r.grouping for r in batch]).astype(np.int32)).to(
+                    device=D.device, non_blocking=False)
+                results = pm.permanova_test_batch(ctx.handle, D, D.shape[0], D.stride(0), g,
+                                                  len(batch), head.n_groups, head.n_perms,
+                                                  [r.seed for r in batch],
+                                                  stream=stream.cuda_stream)
+            for r, res in zip(batch, results):
+                r.result = res
         except Exception as e:  # reported per request; the server keeps running
-            req.error = str(e)
+            for r in batch:
+                r.error = str(e)
         finally:
-            req.t_done = time.perf_counter()
+            t1 = time.perf_counter()
             with self.cv:
-                self.in_use -= req._need
-                self.completed.append(req)
+                for r in batch:
+                    r.t_done = t1
+                    r.batch_size = len(batch)
+                    self.in_use -= r._need
+                    self.completed.append(r)
                 self.cv.notify_all()
             self.free_slots.put(slot)
-            req.done.set()
+            for r in batch:
+                r.done.set()
 
     def close(self):
         with self.cv:

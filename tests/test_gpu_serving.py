@@ -77,6 +77,51 @@ def test_results_identical_alone_and_in_the_mix(matrices):
         srv.close()
 
 
+def test_batch_equals_single_tests(matrices):
+    import paper_2505_04556_gb300 as pm
+    mats, hosts = matrices
+    n = hosts[1].shape[0]
+    labs = [synth.observed_labels(synth.largest_remainder_sizes(n, [3, 2, 1 + k]), 40 + k)
+            for k in range(5)]
+    seeds = [7 + 3 * k for k in range(5)]
+    with pm.Context(0) as ctx:
+        single = [ctx.test(mats[1], torch.from_numpy(l).cuda(), 3, 199, s) for l, s in zip(labs, seeds)]
+        g = torch.from_numpy(np.stack(labs)).cuda()
+        out = torch.empty((5, 200), dtype=torch.float64, device="cuda")
+        batch = pm.permanova_test_batch(ctx.handle, mats[1], n, n, g, 5, 3, 199, seeds, out)
+    for a, b in zip(single, batch):
+        assert a == b
+    ref = oracle.permanova_test(hosts[1], labs[2], 3, 199, seeds[2])
+    np.testing.assert_allclose(out[2].cpu().numpy(), ref["s_W"], rtol=1e-5)
+
+
+def test_compatible_requests_are_batched(matrices):
+    from paper_2505_04556_gb300.serve import Request, Server
+    mats, hosts = matrices
+    n = hosts[2].shape[0]
+
+    def reqs():
+        return [Request(2, synth.observed_labels([n // 2, n - n // 2], 60 + k), 2, 299, seed=500 + k)
+                for k in range(10)]
+    srv = Server(mats, n_slots=1)
+    try:
+        alone = []
+        for r in reqs():
+            srv.submit(r)
+            assert r.done.wait(120) and r.error is None
+            alone.append(r.result)
+        mixed = reqs()
+        for r in mixed:
+            srv.submit(r)
+        for r in mixed:
+            assert r.done.wait(120) and r.error is None, r.error
+    finally:
+        srv.close()
+    assert max(r.batch_size for r in mixed) > 1
+    for r, ref in zip(mixed, alone):
+        assert r.result == ref
+
+
 def test_served_result_matches_oracle(matrices):
     from paper_2505_04556_gb300.serve import Request, Server
     mats, hosts = matrices

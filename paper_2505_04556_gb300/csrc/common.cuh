@@ -90,7 +90,6 @@ cudaError_t launch_validate_labels(const void* labels, int type, uint64_t count,
                                    DevStatus* st, cudaStream_t s);
 cudaError_t launch_reduce_rows(const double* partials, uint32_t rows, uint64_t P, double* out,
                                cudaStream_t s);
-cudaError_t launch_fill_u8(uint8_t* p, uint64_t count, uint8_t v, cudaStream_t s);
 
 // brute force (Algorithm 3 semantics): partials is n_chunks x P
 uint32_t brute_chunks(uint32_t n, int sm_count);

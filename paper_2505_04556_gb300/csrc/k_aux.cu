@@ -151,16 +151,6 @@ cudaError_t launch_widen(const float* in, uint32_t K, double* out, cudaStream_t 
     return launched(1);
 }
 
-__global__ void k_fill_u8(uint8_t* p, uint64_t count, uint8_t v) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = v;
-}
-
-cudaError_t launch_fill_u8(uint8_t* p, uint64_t count, uint8_t v, cudaStream_t s) {
-    k_fill_u8<<<152 * 4, 256, 0, s>>>(p, count, v);
-    return launched(1);
-}
-
 // ---------------------------------------------------------------------------
 // Permutations for the test (Sec. 1).  Counter-based Philox4x32-10 (Salmon,
 // Moraes, Dror & Shaw, SC'11): 10 rounds of the 4x32 Philox S-box (two

@@ -42,8 +42,6 @@ struct permanova_ctx {
     size_t arena_size = 0;
     DevStatus* status = nullptr;        // device error word
     DevStatus* status_host = nullptr;   // pinned mirror
-    TestScalars* scalars = nullptr;     // device
-    TestScalars* scalars_host = nullptr;
     // profiling
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -344,8 +342,6 @@ int permanova_create(int device, size_t hbm_budget_bytes, permanova_ctx** out) {
     cudaError_t e = cudaMalloc(&ctx->status, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->status_host, sizeof(DevStatus));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->scalars, sizeof(TestScalars));
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->scalars_host, sizeof(TestScalars));
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "context allocation");
         permanova_destroy(ctx);
@@ -366,8 +362,6 @@ void permanova_destroy(permanova_ctx* ctx) {
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->status) cudaFree(ctx->status);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
-        if (ctx->scalars) cudaFree(ctx->scalars);
-        if (ctx->scalars_host) cudaFreeHost(ctx->scalars_host);
     }
     delete ctx;
 }

@@ -34,7 +34,7 @@ import numpy as np
 import paper_2505_04556_gb300 as pm
 
 
-@dataclass
+@dataclass(eq=False)   # requests compare by identity (they hold label arrays)
 class Request:
     matrix_id: int
     grouping: object          # host int32 labels (numpy)

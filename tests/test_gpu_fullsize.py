@@ -1,0 +1,84 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py
+times (default kernel plan, uint8 label rows, the benchmark's batch sizes).
+
+* n = 1,000 / 999 rows and n = 20,000 / 3,999 rows: sampled rows against the
+  FP64 oracle (Algorithm 1) one by one.
+* n = 50,000 Bray-Curtis / 8,192 rows: sampled rows against the oracle.
+* n = 100,000 / 8,192 rows (the headline workload): 512 rows spread over
+  the launch against Huygens' identity for Euclidean distances, s_W =
+  sum_g sum_{i in g} |x_i - mu_g|^2 computed from the generating points in
+  FP64 (a property that holds at any size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2505_04556_gb300 as pm  # noqa: E402
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pm.build()
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+def _run(ctx, cfg, X, n_rows, seed):
+    D = synth.recipe_matrix_device(cfg, X)
+    lab = synth.device_label_rows(cfg["labels"], n_rows, seed, dtype=torch.uint8)
+    w = torch.from_numpy(cfg["w"]).cuda()
+    out = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+    pm.permanova_sW(ctx.handle, D, cfg["n"], cfg["n"], lab, pm.LABEL_U8, cfg["K"], n_rows, w, out)
+    pm.permanova_sync(ctx.handle)
+    return D, lab, out.cpu().numpy()
+
+
+def _oracle_rows(D, lab, cfg, idx):
+    Dh = D.cpu().numpy()
+    rows = lab[idx].cpu().numpy().astype(np.int32)
+    return oracle.sW_alg1(Dh, rows, cfg["K"], cfg["w"].astype(np.float64))
+
+
+@pytest.mark.parametrize("name,n_rows,sample", [("euclid-1k", 999, 999), ("euclid-20k", 3999, 48)])
+def test_full_size_sampled_rows(ctx, name, n_rows, sample):
+    cfg = synth.recipe(name)
+    X = synth.recipe_points(cfg)
+    D, lab, got = _run(ctx, cfg, X, n_rows, 31)
+    idx = np.unique(np.linspace(0, n_rows - 1, sample).astype(int))
+    ref = _oracle_rows(D, lab, cfg, idx)
+    np.testing.assert_allclose(got[idx], ref, rtol=RTOL)
+
+
+def test_full_size_braycurtis_50k(ctx):
+    cfg = synth.recipe("braycurtis-50k")
+    X = synth.recipe_points(cfg)
+    D, lab, got = _run(ctx, cfg, X, 8192, 32)
+    idx = np.array([0, 1, 4095, 8191])
+    ref = _oracle_rows(D, lab, cfg, idx)
+    np.testing.assert_allclose(got[idx], ref, rtol=RTOL)
+
+
+def test_full_size_euclid_100k_huygens(ctx):
+    cfg = synth.recipe("euclid-100k")
+    X = synth.recipe_points(cfg)
+    D, lab, got = _run(ctx, cfg, X, 8192, 33)
+    K, dim = cfg["K"], X.shape[1]
+    # Huygens: s_W = sum_g (sum_{i in g} |x_i|^2 - |sum_{i in g} x_i|^2 / n_g)
+    sq = np.einsum("ij,ij->i", X, X)
+    for r in np.linspace(0, 8191, 512).astype(int):
+        g = lab[r].cpu().numpy().astype(np.int64)
+        cnt = np.bincount(g, minlength=K).astype(np.float64)
+        sums = np.stack([np.bincount(g, weights=X[:, d], minlength=K) for d in range(dim)], axis=1)
+        closed = float(np.sum(np.bincount(g, weights=sq, minlength=K)) -
+                       np.sum(np.einsum("kd,kd->k", sums, sums) / cnt))
+        assert abs(got[r] - closed) <= RTOL * closed, (r, got[r], closed)

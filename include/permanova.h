@@ -161,7 +161,14 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
 /* Same as permanova_sW with HOST buffers: mat (n_dims x ld fp32),
  * groupings, inv_group_sizes and out_sW live in host memory (pinned memory
  * gives full copy speed).  The call copies the inputs to the device, runs
- * s_W, copies the n_perms results back and synchronises `stream`. */
+ * s_W, copies the n_perms results back and synchronises `stream`.  Only the
+ * part of mat that s_W reads is copied: for each 128-row band, rows
+ * [128 b, 128 b + 128) from column 128 b on (about half of the matrix).  The
+ * copies run on a stream of the context, ordered after the work already queued
+ * on `stream`; with the tensor-core form the bands are copied in up to 16
+ * segments and each segment's kernels start as soon as it has landed, so the
+ * copies overlap the computation.  Errors as permanova_sW, plus any error the
+ * device reported (the call synchronises). */
 int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
                       const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
                       const float *inv_group_sizes, double *out_sW, void *stream);

@@ -231,10 +231,9 @@ size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
-            uint8_t* __restrict__ tiles) {
+            uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles) {
     const uint64_t NB = 2ull * n_bands;
-    const uint64_t n_tiles = (uint64_t)n_bands * (n_bands + 1);
-    for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         // band I: largest I with tiles_before_band(I) <= t
         uint32_t lo = 0, hi = n_bands - 1;
         while (lo < hi) {
@@ -283,11 +282,16 @@ k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_b
     }
 }
 
-cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s) {
+cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s,
+                             uint32_t I0, uint32_t I1) {
+    if (I1 > gp.n_bands) I1 = gp.n_bands;
+    if (I0 >= I1) return cudaSuccess;
     const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
-    const uint64_t n_tiles = (uint64_t)gp.n_bands * (gp.n_bands + 1);
+    const uint64_t NB = 2ull * gp.n_bands;
+    const uint64_t t0 = tiles_before_band(I0, NB), t1 = tiles_before_band(I1, NB);
+    const uint64_t n_tiles = t1 - t0;
     const unsigned blocks = (unsigned)(n_tiles < 152ull * 16 ? n_tiles : 152ull * 16);
-    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, (uint8_t*)scratch);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, (uint8_t*)scratch);
     return launched(1);
 }
 
@@ -361,6 +365,7 @@ struct GemmArgs {
     uint32_t ppt;
     uint32_t N;                // MMA N (multiple of 16, <= 256)
     uint32_t drain_kb;         // k-blocks accumulated in TMEM between drains
+    uint32_t I0, I1;           // bands [I0, I1) of this launch
 };
 
 // Bounded wait.  With `obey_abort` the wait also gives up once another role
@@ -454,7 +459,8 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const uint64_t n_units = (uint64_t)a.n_bands * a.n_ptiles;
+    // units (band I0 + u / n_ptiles, label-row tile u % n_ptiles) of this launch's band range
+    const uint64_t n_units = (uint64_t)(a.I1 - a.I0) * a.n_ptiles;
     const uint32_t NB = 2 * a.n_bands;
 
     if (warp == 0) {
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             bool ok = true;
             const uint32_t lab_bytes = a.ppt * g::BK;
             for (uint64_t u = blockIdx.x; u < n_units && ok && !*abort_flag; u += gridDim.x) {
-                const uint32_t I = (uint32_t)(u / a.n_ptiles);
+                const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint64_t q = u % a.n_ptiles;
                 const uint8_t* lab_tile = a.labels + q * NB * (uint64_t)lab_bytes;
                 const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             uint64_t kc = 0, cc = 0;
             bool ok = true;
             for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const uint32_t I = (uint32_t)(u / a.n_ptiles);
+                const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint32_t nkb = NB - 2 * I;
                 for (uint32_t c0 = 0; c0 < nkb && ok; c0 += a.drain_kb, ++cc) {
                     const uint32_t b = (uint32_t)(cc & 1);
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         uint32_t epi_phase = 0;
         bool ok = true;
         for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const uint32_t I = (uint32_t)(u / a.n_ptiles);
+            const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
             // the group weights of this thread's two columns (label row p0 + c/K, group c%K)
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         uint64_t kc = 0;
         bool ok = true;
         for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const uint32_t I = (uint32_t)(u / a.n_ptiles);
+            const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t k = 0; k < nkb; ++k, ++kc) {
                 const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
@@ -709,7 +715,10 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 }
 
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
-                             double* partials, DevStatus* st, int sm_count, cudaStream_t s) {
+                             double* partials, DevStatus* st, int sm_count, cudaStream_t s,
+                             uint32_t I0, uint32_t I1) {
+    if (I1 > gp.n_bands) I1 = gp.n_bands;
+    if (I0 >= I1) return cudaSuccess;
     GemmArgs a;
     a.tiles = (const uint8_t*)scratch;
     a.labels = (const uint8_t*)pr.labels;
@@ -726,6 +735,8 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     a.N = (a.ppt * pr.K + 15) / 16 * 16;
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
     // accumulation length in TMEM between FP64 drains (tuning/testing override)
+    a.I0 = I0;
+    a.I1 = I1;
     a.drain_kb = g::DRAIN_KB;
     if (const char* env = getenv("PERMANOVA_GEMM_DRAIN")) {
         const int v = atoi(env);
@@ -735,7 +746,7 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     cudaError_t e = cudaFuncSetAttribute(k_gemm_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g::SMEM_ALLOC);
     if (e != cudaSuccess) return e;
-    const uint64_t n_units = (uint64_t)gp.n_bands * gp.n_ptiles;
+    const uint64_t n_units = (uint64_t)(I1 - I0) * gp.n_ptiles;
     const unsigned grid = (unsigned)(n_units < (uint64_t)sm_count ? n_units : (uint64_t)sm_count);
     k_gemm_main<<<grid, g::THREADS, g::SMEM_ALLOC, s>>>(a);
     return launched(1);

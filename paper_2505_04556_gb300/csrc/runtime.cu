@@ -47,6 +47,9 @@ struct permanova_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     uint64_t launch_mark = 0;
     int last_form = 0;
+    // host entry point: copies run on their own stream, ordered by events
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
 };
 
 namespace {
@@ -87,6 +90,7 @@ struct DeviceGuard {
 };
 
 constexpr size_t kAlign = 256;
+constexpr uint32_t kHostSegments = 16;   // band segments of the host entry point's copy pipeline
 size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 // Scratch carve-up for one s_W call.
@@ -239,12 +243,30 @@ void profile_clear(permanova_ctx* ctx) {
     ctx->launch_mark = kernel_launch_count();
 }
 
+// Inputs that arrive on the device while the path runs (host entry point):
+// segment k covers the 128-row bands [band[k], band[k+1]) of D and is on the
+// device once seg_ready[k] has fired; labels and weights once lab_ready has.
+struct Arrival {
+    cudaEvent_t lab_ready = nullptr;
+    std::vector<uint32_t> band;
+    std::vector<cudaEvent_t> seg_ready;
+};
+
 // The s_W path on device buffers; the arena is already large enough.
 // `wf` (device fp32 inv_group_sizes) is widened into the layout's FP64 slot;
 // with wf == NULL, pr.w (FP64, possibly several weight sets) is used, or the
-// layout's slot when pr.w is NULL.
-int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s) {
+// layout's slot when pr.w is NULL.  With `arr`, each step waits for the inputs
+// it reads; the GEMM form then prepares and runs band segment k as soon as
+// segment k has arrived, so the copies of later segments overlap the tensor-core
+// work on earlier ones.
+int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s,
+           const Arrival* arr = nullptr) {
     char* base = static_cast<char*>(ctx->arena);
+    if (arr) CK(cudaStreamWaitEvent(s, arr->lab_ready, 0), "wait for labels");
+    // all of D: the CUDA-core forms read every band in one launch
+    auto wait_all_rows = [&]() -> cudaError_t {
+        return arr ? cudaStreamWaitEvent(s, arr->seg_ready.back(), 0) : cudaSuccess;
+    };
     double* partials = reinterpret_cast<double*>(base + L.part_off);
     double* wd = reinterpret_cast<double*>(base + L.w_off);
     if (wf) {
@@ -257,6 +279,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
     if (L.form == PERMANOVA_FORM_BRUTE) {
         CK(launch_validate_labels(pr.labels, pr.label_type, (uint64_t)pr.n * pr.P, pr.K, ctx->status, s),
            "validate labels");
+        CK(wait_all_rows(), "wait for the matrix");
         int rc = profile_begin(ctx, s);
         if (rc) return rc;
         CK(launch_brute(pr, L.part_rows, partials, ctx->status, s), "brute-force kernel");
@@ -281,6 +304,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                "validate labels");
         }
         if (L.form == PERMANOVA_FORM_PERMBLOCK) {
+            CK(wait_all_rows(), "wait for the matrix");
             int rc = profile_begin(ctx, s);
             if (rc) return rc;
             CK(launch_permblock_internal(q, L.lstride, partials, ctx->status, s), "perm-block kernel");
@@ -289,12 +313,23 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
         } else {
             const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P);
             void* gs = base + L.gemm_off;
-            CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
-            int rc = profile_begin(ctx, s);
-            if (rc) return rc;
-            CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s), "GEMM kernel");
-            rc = profile_end(ctx, s);
-            if (rc) return rc;
+            if (!arr) {
+                CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
+                int rc = profile_begin(ctx, s);
+                if (rc) return rc;
+                CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s), "GEMM kernel");
+                rc = profile_end(ctx, s);
+                if (rc) return rc;
+            } else {
+                for (size_t k = 0; k + 1 < arr->band.size(); ++k) {
+                    CK(cudaStreamWaitEvent(s, arr->seg_ready[k], 0), "wait for a matrix segment");
+                    CK(launch_gemm_prep(q, gp, gs, s, arr->band[k], arr->band[k + 1]),
+                       "GEMM operand preparation");
+                    CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s, arr->band[k],
+                                        arr->band[k + 1]),
+                       "GEMM kernel");
+                }
+            }
         }
     }
     CK(launch_reduce_rows(partials, L.part_rows, pr.P, pr.out, s), "reduce partials");
@@ -360,6 +395,8 @@ void permanova_destroy(permanova_ctx* ctx) {
         for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
         ctx->graph_cache.clear();
         if (ctx->arena) cudaFree(ctx->arena);
+        for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
         if (ctx->status) cudaFree(ctx->status);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
     }
@@ -558,8 +595,10 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     SWLayout L;
     rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
     if (rc) return rc;
-    // staging for the inputs and the output after the s_W scratch
-    const size_t mat_bytes = (size_t)n * ld * sizeof(float);
+    // staging for the inputs and the output after the s_W scratch; the staged
+    // matrix has a row stride of n rounded up to 4 floats (16-byte rows)
+    const uint64_t ldd = (n + 3ull) / 4 * 4;
+    const size_t mat_bytes = (size_t)n * ldd * sizeof(float);
     const size_t lab_bytes = (size_t)n * P * label_bytes(label_type);
     size_t off = L.total;
     const size_t mat_off = off;
@@ -573,16 +612,63 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     rc = ensure_arena(ctx, off);
     if (rc) return rc;
     char* base = static_cast<char*>(ctx->arena);
-    CK(cudaMemcpyAsync(base + mat_off, mat, mat_bytes, cudaMemcpyHostToDevice, s), "copy mat");
-    CK(cudaMemcpyAsync(base + lab_off, groupings, lab_bytes, cudaMemcpyHostToDevice, s), "copy labels");
-    CK(cudaMemcpyAsync(base + w_off, w, (size_t)K * sizeof(float), cudaMemcpyHostToDevice, s),
+
+    // Copies run on the context's copy stream, after the work already queued on
+    // `stream` (which may still read the arena).  Only the strict upper
+    // triangle of D is read by every form, so each 128-row band of rows
+    // [128 I, 128 I + 128) is copied from column 128 I on: about half of D.
+    // With the GEMM form the bands go in segments of equal area, each with its
+    // own event, and segment k's tensor-core work starts once it has landed.
+    const uint32_t n_bands = (n + 127) / 128;
+    const uint32_t n_seg = L.form == PERMANOVA_FORM_GEMM ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
+    if (!ctx->copy_stream)
+        CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "create copy stream");
+    while (ctx->copy_events.size() < kHostSegments + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create copy event");
+        ctx->copy_events.push_back(e);
+    }
+    cudaStream_t cs = ctx->copy_stream;
+    Arrival arr;
+    arr.lab_ready = ctx->copy_events[0];
+    cudaEvent_t start = ctx->copy_events[1];
+    CK(cudaEventRecord(start, s), "record start");
+    CK(cudaStreamWaitEvent(cs, start, 0), "order copies after earlier work");
+    CK(cudaMemcpyAsync(base + lab_off, groupings, lab_bytes, cudaMemcpyHostToDevice, cs), "copy labels");
+    CK(cudaMemcpyAsync(base + w_off, w, (size_t)K * sizeof(float), cudaMemcpyHostToDevice, cs),
        "copy weights");
+    CK(cudaEventRecord(arr.lab_ready, cs), "record labels");
+    // segment boundaries: equal shares of the triangle's band area
+    auto band_area = [&](uint32_t I) -> double {
+        const uint32_t r0 = 128 * I, r1 = std::min(n, r0 + 128);
+        return (double)(r1 - r0) * (double)(n - r0);
+    };
+    double total = 0.0;
+    for (uint32_t I = 0; I < n_bands; ++I) total += band_area(I);
+    arr.band.push_back(0);
+    double acc = 0.0;
+    float* dmat = reinterpret_cast<float*>(base + mat_off);
+    for (uint32_t I = 0; I < n_bands; ++I) {
+        const uint32_t r0 = 128 * I, r1 = std::min(n, r0 + 128);
+        CK(cudaMemcpy2DAsync(dmat + (uint64_t)r0 * ldd + r0, ldd * sizeof(float), mat + (uint64_t)r0 * ld + r0,
+                             ld * sizeof(float), (size_t)(n - r0) * sizeof(float), r1 - r0,
+                             cudaMemcpyHostToDevice, cs),
+           "copy matrix band");
+        acc += band_area(I);
+        const size_t k = arr.band.size() - 1;   // segment being filled
+        if (I + 1 == n_bands || acc >= total * (double)(k + 1) / n_seg) {
+            cudaEvent_t e = ctx->copy_events[2 + k];
+            CK(cudaEventRecord(e, cs), "record segment");
+            arr.seg_ready.push_back(e);
+            arr.band.push_back(I + 1);
+        }
+    }
     // the staged label buffer is 256-byte aligned: re-plan so the direct path can be taken
-    rc = layout_for(ctx, L.form, n, ld, base + lab_off, label_type, K, P, &L);
+    rc = layout_for(ctx, L.form, n, ldd, base + lab_off, label_type, K, P, &L);
     if (rc) return rc;
-    SWProblem pr{reinterpret_cast<const float*>(base + mat_off), n, ld, base + lab_off, label_type, K,
+    SWProblem pr{reinterpret_cast<const float*>(dmat), n, ldd, base + lab_off, label_type, K,
                  P, nullptr, reinterpret_cast<double*>(base + out_off)};
-    rc = run_sW(ctx, L, pr, reinterpret_cast<const float*>(base + w_off), s);
+    rc = run_sW(ctx, L, pr, reinterpret_cast<const float*>(base + w_off), s, &arr);
     if (rc) return rc;
     CK(cudaMemcpyAsync(out, base + out_off, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, s),
        "copy results");

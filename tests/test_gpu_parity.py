@@ -272,3 +272,32 @@ def test_host_entry_point(ctx):
     pm.permanova_sW_host(ctx.handle, np.ascontiguousarray(D), 321, 321, lab, pm.LABEL_U8, 4, 50,
                          np.ascontiguousarray(w), out)
     np.testing.assert_allclose(out, ref, rtol=RTOL)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n,ld", [(1000, 1003), (2177, 2177)])
+def test_host_entry_segments(ctx, form, n, ld):
+    """The host entry point copies only the band trapezoids of D (the lower
+    triangle below them never reaches the device) and, with the tensor-core
+    form, runs band segments as they land: results equal the device entry
+    point's bit for bit (on a device copy with the staged row stride, n
+    rounded up to 4 floats: the brute-force kernel's summation order depends
+    on whether rows are 16-byte aligned) and the oracle's within tolerance."""
+    K, P = 5, 70
+    D, rows, w = _case(n, K, P, seed=37)
+    Dp = np.full((n, ld), np.nan, dtype=np.float32)
+    Dp[:, :n] = D
+    Dp[np.tril_indices(n)] = np.nan
+    lab = np.ascontiguousarray(rows.astype(np.uint8))
+    out = np.zeros(P, dtype=np.float64)
+    ctx.set_form(form)
+    try:
+        pm.permanova_sW_host(ctx.handle, Dp, n, ld, lab, pm.LABEL_U8, K, P,
+                             np.ascontiguousarray(w, dtype=np.float32), out)
+    finally:
+        ctx.set_form(pm.FORM_AUTO)
+    dev = _run_sW(ctx, D, rows, K, w, form, pm.LABEL_U8, ld=(n + 3) // 4 * 4)
+    np.testing.assert_array_equal(out, dev)
+    idx = np.arange(0, P, 7)
+    ref = oracle.sW_alg1(D, rows[idx], K, w.astype(np.float64))
+    np.testing.assert_allclose(out[idx], ref, rtol=RTOL)

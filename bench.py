@@ -103,7 +103,7 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -114,12 +114,18 @@ class ClockSampler:
                 smax.append(float(parts[1]))
             except ValueError:
                 continue
+            try:
+                power.append(float(parts[2]))
+            except ValueError:
+                pass
             for nm, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(power) if power else None,
+                "power_w_max": max(power) if power else None}
 
 
 def gpu_query_id(torch, dev: int) -> str | None:

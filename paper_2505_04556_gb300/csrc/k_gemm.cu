@@ -23,14 +23,16 @@
 // swizzled layout, so one bulk copy (TMA engine) moves both planes.  Entries
 // with j <= i, i >= n or j >= n are zero.
 //
-// Kernel.  Persistent, one CTA per SM, 12 warps:
-//   warp 0       bulk-copies the A tiles and the 64-column label slices of the
-//                tile's label rows into a 3-stage shared-memory ring;
+// Kernel.  Persistent, one CTA per SM, 16 warps:
+//   warp 0       bulk-copies the A tiles into a 4-stage ring and the 64-column
+//                label slices of the tile's label rows into a label ring that
+//                runs up to 16 k-blocks ahead;
 //   warp 1       owns 512 TMEM columns (two 128 x 256 FP32 accumulators) and
 //                issues the tcgen05.mma instructions (one thread);
 //   warps 4-7    drain the accumulators (tcgen05.ld), keep column
 //                (p, g_p(i)) of each row, weight it, reduce over rows;
-//   warps 8-11   build the one-hot B tile of each stage from the labels.
+//   warps 8-15   build the one-hot B tile (2-stage ring) from the labels, one
+//                B row per thread.
 // Work unit = (band I, tile of up to 64 label rows), band-major so the CTAs
 // running together share a band and read its A tiles from L2.
 // Every wait is bounded; on timeout the kernel records DEV_TIMEOUT, lets the
@@ -49,26 +51,30 @@ constexpr int BM = 128;             // band height (MMA M)
 constexpr int BK = 64;              // k-block width (one 128-byte swizzle atom of BF16)
 constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
 constexpr int PPT_MAX = 64;         // label rows per tile
-constexpr int NST = 3;              // pipeline stages
+constexpr int NA = 4;               // A-tile stages (bulk copies in flight)
+constexpr int NBS = 2;              // one-hot B-tile stages (built on chip)
 constexpr int DRAIN_KB = 16;        // default k-blocks per accumulator chunk
 constexpr int PREFETCH_KB = 8;      // L2 prefetch distance along the band (k-blocks)
-constexpr int THREADS = 384;
+constexpr int THREADS = 512;        // 16 warps
+constexpr int BUILDERS = 256;       // warps 8-15: one B row per thread
 constexpr uint32_t PLANE_BYTES = BM * BK * 2;             // 16 KB
 constexpr uint32_t TILE_BYTES = 2 * PLANE_BYTES;          // hi + lo planes: 32 KB
 constexpr uint32_t A_BYTES = TILE_BYTES;
 constexpr uint32_t B_BYTES = NMAX * BK * 2;               // 32 KB
-constexpr uint32_t LAB_BYTES = PPT_MAX * BK;              // 4 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES + LAB_BYTES;   // 68 KB
-constexpr uint32_t OFF_LABROWS = NST * STAGE_BYTES;
-constexpr uint32_t OFF_RED = OFF_LABROWS + PPT_MAX * BM;          // [2][4][NMAX] float
-constexpr uint32_t OFF_ACC64 = OFF_RED + 2 * 4 * NMAX * 4;        // [NMAX] double
-constexpr uint32_t OFF_BAR = OFF_ACC64 + NMAX * 8;
-constexpr uint32_t N_BARS = 4 * NST + 6;
+constexpr uint32_t OFF_B = NA * A_BYTES;                  // B ring after the A ring
+constexpr uint32_t LRING_BYTES = 16384;                   // label ring (ppt x 64 bytes per slot)
+constexpr uint32_t NL_MAX = 16;                           // label slots at most
+constexpr uint32_t OFF_LRING = OFF_B + NBS * B_BYTES;
+constexpr uint32_t OFF_LABROWS = OFF_LRING + LRING_BYTES;          // [PPT_MAX][BM] uint8
+constexpr uint32_t OFF_ACC64 = OFF_LABROWS + PPT_MAX * BM;         // [4][NMAX] double
+constexpr uint32_t OFF_BAR = OFF_ACC64 + 4 * NMAX * 8;
+constexpr uint32_t N_BARS = 2 * NA + 2 * NBS + 2 * NL_MAX + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
 constexpr uint32_t SMEM_ALLOC = SMEM_BYTES + 1024;       // room to align the base to 1 KB
 constexpr long long WAIT_LIMIT = 4000000000LL;           // clock cycles (~2 s)
 static_assert(SMEM_ALLOC <= 232448, "shared memory budget");
+static_assert(PPT_MAX * BK <= LRING_BYTES, "one label slot must fit the ring");
 }  // namespace g
 
 // ---------------------------------------------------------------------------
@@ -173,6 +179,14 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], uint32_t lane)
         }
     }
     return v[0];
+}
+
+// Packed BF16 equality: each 16-bit half of the result is 1.0 (0x3F80) where
+// the halves of a and b are equal values, else 0.0.
+__device__ __forceinline__ uint32_t bf16x2_eq(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("set.eq.bf16x2.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
@@ -350,6 +364,18 @@ cudaError_t launch_repack_gemm(const void* in, int in_type, uint32_t n, uint64_t
 // ---------------------------------------------------------------------------
 // the persistent tensor-core kernel
 // ---------------------------------------------------------------------------
+// Position in a ring of barrier-guarded slots: slot index and the parity of
+// the slot's current phase (kept incrementally: no division per step).
+struct Ring {
+    uint32_t idx = 0, phase = 0;
+    __device__ __forceinline__ void next(uint32_t n) {
+        if (++idx == n) {
+            idx = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
 struct GemmArgs {
     const uint8_t* tiles;      // prepared A tiles
     const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
@@ -410,30 +436,40 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + g::OFF_BAR);
-    uint64_t* full = bars;                        // [NST] A tile landed
-    uint64_t* ready = bars + g::NST;              // [NST] B tile built
-    uint64_t* empty = bars + 2 * g::NST;          // [NST] MMAs of the stage done
-    uint64_t* acc_full = bars + 3 * g::NST;       // [2]
-    uint64_t* acc_empty = bars + 3 * g::NST + 2;  // [2]
-    uint64_t* epi_bar = bars + 3 * g::NST + 4;    // epilogue warps meet here once per chunk
-    uint64_t* mma_done = bars + 3 * g::NST + 5;   // final commit of the MMA thread
-    uint64_t* lfull = bars + 3 * g::NST + 6;      // [NST] label slice landed (B can be built
-                                                  // while the A tile is still in flight)
+    uint64_t* full = bars;                          // [NA] A tile landed
+    uint64_t* aempty = full + g::NA;                // [NA] MMAs reading the A stage done
+    uint64_t* ready = aempty + g::NA;               // [NBS] B tile built
+    uint64_t* bempty = ready + g::NBS;              // [NBS] MMAs reading the B stage done
+    uint64_t* lfull = bempty + g::NBS;              // [NL_MAX] label slot landed
+    uint64_t* lempty = lfull + g::NL_MAX;           // [NL_MAX] label slot read by the builders
+    uint64_t* acc_full = lempty + g::NL_MAX;        // [2]
+    uint64_t* acc_empty = acc_full + 2;             // [2]
+    uint64_t* epi_bar = acc_full + 4;               // epilogue warps meet here twice per unit
+    uint64_t* mma_done = acc_full + 5;              // final commit of the MMA thread
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
+    uint8_t* lring = sm + g::OFF_LRING;                          // [NL][ppt][64] labels
     uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
-    float* red = reinterpret_cast<float*>(sm + g::OFF_RED);      // [2][4][NMAX]
-    double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);
+    double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);  // [4][NMAX]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevStatus* st = a.st;
+    const uint32_t lab_bytes = a.ppt * g::BK;                    // one label slot
+    uint32_t NL = g::LRING_BYTES / lab_bytes;
+    if (NL > g::NL_MAX) NL = g::NL_MAX;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < g::NST; ++s) {
+        for (int s = 0; s < g::NA; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&lfull[s], 1);
-            mbar_init(&ready[s], 128);
-            mbar_init(&empty[s], 1);
+            mbar_init(&aempty[s], 1);
+        }
+        for (int s = 0; s < g::NBS; ++s) {
+            mbar_init(&ready[s], g::BUILDERS);
+            mbar_init(&bempty[s], 1);
+        }
+        for (uint32_t l = 0; l < g::NL_MAX; ++l) {
+            mbar_init(&lfull[l], 1);
+            mbar_init(&lempty[l], g::BUILDERS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -445,10 +481,8 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // B rows beyond ppt*K stay zero in every stage
-    for (uint32_t e = threadIdx.x; e < g::NST * (g::B_BYTES / 16); e += blockDim.x) {
-        const uint32_t s = e / (g::B_BYTES / 16), o = e % (g::B_BYTES / 16);
-        *reinterpret_cast<uint4*>(sm + s * g::STAGE_BYTES + g::A_BYTES + o * 16) = make_uint4(0, 0, 0, 0);
-    }
+    for (uint32_t e = threadIdx.x; e < g::NBS * (g::B_BYTES / 16); e += blockDim.x)
+        *reinterpret_cast<uint4*>(sm + g::OFF_B + e * 16) = make_uint4(0, 0, 0, 0);
     if (warp == 1) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
@@ -465,46 +499,59 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
+        // Two streams in the same (unit, k-block) order: label slices run up to
+        // NL k-blocks ahead in their own ring (the builders never wait for a
+        // label copy), A tiles follow the NA-stage ring.
         if (lane == 0) {
-            uint64_t kc = 0;
-            int64_t last_round[g::NST] = {-1, -1, -1};
+            uint64_t kc = 0;                 // A stream position
+            uint64_t lk = 0;                 // label stream position
+            Ring ra, rl;                     // A ring and label ring slots
+            uint64_t lu = blockIdx.x;        // label stream unit and k-block
+            uint32_t lkb = lu < n_units ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
             bool ok = true;
-            const uint32_t lab_bytes = a.ppt * g::BK;
             for (uint64_t u = blockIdx.x; u < n_units && ok && !*abort_flag; u += gridDim.x) {
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
-                const uint64_t q = u % a.n_ptiles;
-                const uint8_t* lab_tile = a.labels + q * NB * (uint64_t)lab_bytes;
                 const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
                 for (uint32_t kb = 2 * I; kb < NB; ++kb, ++kc, tile += g::TILE_BYTES) {
-                    const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
-                    if (!wait_bar(&empty[s], (r & 1) ^ 1, abort_flag, st, 1)) { ok = false; break; }
-                    uint8_t* stg = sm + s * g::STAGE_BYTES;
-                    // the tile's label slice for this k-block (one contiguous block) first,
-                    // on its own barrier, so the B builders need not wait for the A tile
-                    mbar_arrive_expect_tx(&lfull[s], lab_bytes);
-                    bulk_g2s(stg + g::A_BYTES + g::B_BYTES, lab_tile + (uint64_t)kb * lab_bytes, lab_bytes,
-                             &lfull[s]);
-                    mbar_arrive_expect_tx(&full[s], g::A_BYTES);
-                    bulk_g2s(stg, tile, g::A_BYTES, &full[s]);
-                    last_round[s] = r;
+                    // keep the label ring full: slices up to position kc + NL - 1
+                    while (lu < n_units && lk < kc + NL) {
+                        if (!wait_bar(&lempty[rl.idx], rl.phase ^ 1, abort_flag, st, 12)) { ok = false; break; }
+                        const uint64_t q = lu % a.n_ptiles;
+                        mbar_arrive_expect_tx(&lfull[rl.idx], lab_bytes);
+                        bulk_g2s(lring + rl.idx * lab_bytes, a.labels + (q * NB + lkb) * (uint64_t)lab_bytes,
+                                 lab_bytes, &lfull[rl.idx]);
+                        ++lk;
+                        rl.next(NL);
+                        if (++lkb == NB) {
+                            lu += gridDim.x;
+                            lkb = lu < n_units ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
+                        }
+                    }
+                    if (!ok) break;
+                    if (!wait_bar(&aempty[ra.idx], ra.phase ^ 1, abort_flag, st, 1)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[ra.idx], g::A_BYTES);
+                    bulk_g2s(sm + ra.idx * g::A_BYTES, tile, g::A_BYTES, &full[ra.idx]);
+                    ra.next(g::NA);
                     // pull a tile further along the band into L2, so the copies that
                     // reach it (this CTA's and the other CTAs on the same band) hit L2
                     if (kb + g::PREFETCH_KB < NB)
                         bulk_prefetch_l2(tile + (uint64_t)g::PREFETCH_KB * g::TILE_BYTES, g::TILE_BYTES);
                 }
             }
-            // every issued copy must land before the CTA exits
-            for (int s = 0; s < g::NST; ++s)
-                if (last_round[s] >= 0) {
-                    wait_bar(&lfull[s], (uint32_t)last_round[s] & 1, abort_flag, st, 7, false);
-                    wait_bar(&full[s], (uint32_t)last_round[s] & 1, abort_flag, st, 7, false);
-                }
+            // every issued copy must land before the CTA exits: a slot below the ring's
+            // next index was last used in the current phase, one at or above it in the
+            // previous phase (if it was used at all)
+            for (uint32_t l = 0; l < NL; ++l)
+                if (lk > l) wait_bar(&lfull[l], l < rl.idx ? rl.phase : rl.phase ^ 1, abort_flag, st, 7, false);
+            for (uint32_t s = 0; s < (uint32_t)g::NA; ++s)
+                if (kc > s) wait_bar(&full[s], s < ra.idx ? ra.phase : ra.phase ^ 1, abort_flag, st, 7, false);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(g::BM, a.N);
-            uint64_t kc = 0, cc = 0;
+            uint64_t cc = 0;
+            Ring ra, rb;
             bool ok = true;
             for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
@@ -518,23 +565,25 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + b * g::NMAX;
                     const uint32_t c1 = min(nkb, c0 + a.drain_kb);
-                    for (uint32_t k = c0; k < c1; ++k, ++kc) {
-                        const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
-                        if (!wait_bar(&full[s], r & 1, abort_flag, st, 3) ||
-                            !wait_bar(&ready[s], r & 1, abort_flag, st, 4)) {
+                    for (uint32_t k = c0; k < c1; ++k) {
+                        if (!wait_bar(&full[ra.idx], ra.phase, abort_flag, st, 3) ||
+                            !wait_bar(&ready[rb.idx], rb.phase, abort_flag, st, 4)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(sm + s * g::STAGE_BYTES);
-                        const uint32_t sb = sa + g::A_BYTES;
+                        const uint32_t sa = smem_u32(sm + ra.idx * g::A_BYTES);
+                        const uint32_t sb = smem_u32(sm + g::OFF_B + rb.idx * g::B_BYTES);
 #pragma unroll
                         for (int kk = 0; kk < g::BK / 16; ++kk) {
                             const uint64_t bd = sw128_desc(sb + kk * 32);
                             mma_bf16(d_tmem, sw128_desc(sa + kk * 32), bd, idesc, (k > c0 || kk > 0) ? 1u : 0u);
                             mma_bf16(d_tmem, sw128_desc(sa + g::PLANE_BYTES + kk * 32), bd, idesc, 1u);
                         }
-                        mma_commit(&empty[s]);
+                        mma_commit(&aempty[ra.idx]);
+                        mma_commit(&bempty[rb.idx]);
+                        ra.next(g::NA);
+                        rb.next(g::NBS);
                     }
                     if (ok) mma_commit(&acc_full[b]);
                 }
@@ -545,14 +594,16 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         }
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------ epilogue
+        // Lane l of warp q4 owns accumulator columns c = 32 grp + l (grp = 0..7)
+        // for rows 32 q4 .. 32 q4 + 31: per drained chunk it sums its rows'
+        // selected values over the warp (FP32 butterfly), weights the column sum
+        // and accumulates it in FP64.  The four warps' FP64 column sums are
+        // added in a fixed order once per unit.
         const uint32_t et = threadIdx.x - 128;     // 0..127
         const uint32_t q4 = warp - 4;              // TMEM lane quarter
         const uint32_t row = q4 * 32 + lane;       // row within the band
         const uint32_t K = a.K;
         const uint32_t used = a.ppt * K;           // accumulator columns that carry a (p, g)
-        // the two accumulator columns this thread finalises, and their group weights
-        const uint32_t cA = et, cB = et + 128;
-        double accA = 0.0, accB = 0.0;
         uint64_t cc = 0;
         uint32_t epi_phase = 0;
         bool ok = true;
@@ -560,15 +611,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
-            // the group weights of this thread's two columns (label row p0 + c/K, group c%K)
-            const double wA = (cA < used && cA / K < nlab)
-                                  ? __ldg(weight_row(a.w, p0 + cA / K, a.w_set_rows, K) + cA % K) : 0.0;
-            const double wB = (cB < used && cB / K < nlab)
-                                  ? __ldg(weight_row(a.w, p0 + cB / K, a.w_set_rows, K) + cB % K) : 0.0;
             // the band's row labels for the tile's label rows: k-blocks 2I and 2I+1 of
             // the tile's label blocks, loaded cooperatively (16 bytes per thread-step)
             {
-                const uint32_t lab_bytes = a.ppt * g::BK;
                 const uint8_t* lb = a.labels + ((u % a.n_ptiles) * NB + 2ull * I) * lab_bytes;
                 const uint32_t per_half = a.ppt * (g::BK / 16);
                 for (uint32_t idx = et; idx < 2 * per_half; idx += 128) {
@@ -603,12 +648,20 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     msk[grp] = m;
                 }
             }
+            // the group weights of this lane's columns (label row p0 + c/K, group c%K)
+            double wc[g::NMAX / 32], acc[g::NMAX / 32];
+#pragma unroll
+            for (int grp = 0; grp < g::NMAX / 32; ++grp) {
+                const uint32_t c = 32u * grp + lane;
+                wc[grp] = (c < used && c / K < nlab)
+                              ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) : 0.0;
+                acc[grp] = 0.0;
+            }
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t c0 = 0; c0 < nkb; c0 += a.drain_kb, ++cc) {
                 const uint32_t b = (uint32_t)(cc & 1);
                 if (!wait_bar(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
                 tc_fence_after();
-                float* redc = red + (cc & 1) * 4 * g::NMAX;
                 const uint32_t taddr = tmem + ((q4 * 32u) << 16) + b * g::NMAX;
 #pragma unroll
                 for (int grp = 0; grp < g::NMAX / 32; ++grp) {
@@ -621,85 +674,85 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 #pragma unroll
                         for (int k = 0; k < 32; ++k) v[k] = (msk[grp] >> k) & 1u ? __uint_as_float(r[k]) : 0.f;
                         // column 32 grp + lane summed over the warp's 32 rows
-                        redc[q4 * g::NMAX + 32 * grp + lane] = reduce_scatter32(v, lane);
+                        acc[grp] = fma((double)reduce_scatter32(v, lane), wc[grp], acc[grp]);
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[b]);
-                // the four warps' column sums of this chunk, added in a fixed order,
-                // weighted and accumulated in FP64
-                mbar_arrive(epi_bar);
-                if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 9, false)) { ok = false; break; }
-                ++epi_phase;
-                if (cA < used)
-                    accA += (double)((redc[cA] + redc[g::NMAX + cA]) + (redc[2 * g::NMAX + cA] + redc[3 * g::NMAX + cA])) * wA;
-                if (cB < used)
-                    accB += (double)((redc[cB] + redc[g::NMAX + cB]) + (redc[2 * g::NMAX + cB] + redc[3 * g::NMAX + cB])) * wB;
             }
             if (!ok) break;
-            // per label row: the sum of its K columns, in group order
-            acc64[cA] = accA;
-            acc64[cB] = accB;
-            accA = 0.0;
-            accB = 0.0;
+            // per label row: the four warps' column sums, then its K columns in group order
+#pragma unroll
+            for (int grp = 0; grp < g::NMAX / 32; ++grp) acc64[q4 * g::NMAX + 32 * grp + lane] = acc[grp];
             mbar_arrive(epi_bar);
             if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 11, false)) { ok = false; break; }
             ++epi_phase;
             for (uint32_t pp = et; pp < nlab; pp += 128) {
                 double t = 0.0;
-                for (uint32_t gg = 0; gg < K; ++gg) t += acc64[pp * K + gg];
+                for (uint32_t gg = 0; gg < K; ++gg) {
+                    const uint32_t c = pp * K + gg;
+                    t += (acc64[c] + acc64[g::NMAX + c]) + (acc64[2 * g::NMAX + c] + acc64[3 * g::NMAX + c]);
+                }
                 a.partials[(uint64_t)I * a.P + p0 + pp] = t;
             }
         }
     } else if (warp >= 8) {
         // ------------------------------------------------------------ B builders
-        const uint32_t t = threadIdx.x - 256;      // 0..127
+        // Thread t builds row t of every B tile (the one-hot column of label row
+        // t / K and group t % K over the k-block's 64 objects).  A label byte L
+        // becomes the BF16 bit pattern 0x43LL (a distinct finite value for each
+        // of the 256 byte values) by one byte permute per two labels, and one
+        // packed BF16 equality compare against 0x43gg writes 1.0 or 0.0 for both.
+        const uint32_t c = threadIdx.x - 256;      // 0..255
         const uint32_t K = a.K;
         const uint32_t rows_used = a.ppt * K;
-        uint64_t kc = 0;
+        const uint32_t pl = c / K, gg = c - pl * K;
+        const uint32_t key = (0x4300u | gg) * 0x00010001u;   // (0x43gg, 0x43gg)
+        Ring rb, rl;
         bool ok = true;
         for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
             const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint32_t nkb = NB - 2 * I;
-            for (uint32_t k = 0; k < nkb; ++k, ++kc) {
-                const uint32_t s = (uint32_t)(kc % g::NST), r = (uint32_t)(kc / g::NST);
-                if (!wait_bar(&lfull[s], r & 1, abort_flag, st, 6)) { ok = false; break; }
-                uint8_t* B = sm + s * g::STAGE_BYTES + g::A_BYTES;
-                const uint8_t* L = B + g::B_BYTES;
+            for (uint32_t k = 0; k < nkb; ++k) {
+                // the label slice has landed, and the stage's previous B tile is consumed
+                if (!wait_bar(&lfull[rl.idx], rl.phase, abort_flag, st, 6) ||
+                    !wait_bar(&bempty[rb.idx], rb.phase ^ 1, abort_flag, st, 13)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* B = sm + g::OFF_B + rb.idx * g::B_BYTES;
+                const uint8_t* L = lring + rl.idx * lab_bytes;
+                if (c < rows_used) {
+                    // the label row's 64 bytes in four 16-byte chunks, each giving two 16-byte
+                    // chunks of the B row; chunk (q + pl/2) % 4 at step q puts the up to 8
+                    // label rows a warp reads on distinct banks
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t c = t + 128u * h;
-                    if (c < rows_used) {
-                        const uint32_t pl = c / K, gg = c - pl * K;
-                        const uint32_t rep = gg * 0x01010101u;
-                        // the label row's 64 bytes in four 16-byte loads (lanes of a
-                        // quarter-warp read at most two rows: no bank conflicts)
-                        uint32_t lw[16];
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
+                        const uint4 v = *reinterpret_cast<const uint4*>(L + pl * g::BK + ch * 16);
+                        const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint4 v = *reinterpret_cast<const uint4*>(L + pl * g::BK + q * 16);
-                            lw[4 * q] = v.x; lw[4 * q + 1] = v.y; lw[4 * q + 2] = v.z; lw[4 * q + 3] = v.w;
-                        }
-#pragma unroll
-                        for (uint32_t c8 = 0; c8 < 8; ++c8) {
-                            const uint32_t xs[2] = {lw[2 * c8] ^ rep, lw[2 * c8 + 1] ^ rep};
+                        for (int h = 0; h < 2; ++h) {
                             uint32_t o[4];
 #pragma unroll
                             for (int hw = 0; hw < 2; ++hw) {
-                                const uint32_t x = xs[hw];
-                                // 0x80 in every byte of x that is zero (label == g), else 0
-                                const uint32_t nz = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-                                const uint32_t eq = ~nz & 0x80808080u;
-                                // spread bytes to 16-bit halves; 0x80 * 0x7F = 0x3F80 = bf16 1.0
-                                o[2 * hw] = __byte_perm(eq, 0u, 0x4140u) * 0x7Fu;
-                                o[2 * hw + 1] = __byte_perm(eq, 0u, 0x4342u) * 0x7Fu;
+                                const uint32_t x = xs[2 * h + hw];
+                                // labels 0,1 and 2,3 of x as BF16 pairs (0x43L0, 0x43L1), (0x43L2, 0x43L3)
+                                const uint32_t lo = __byte_perm(x, 0x43u, 0x4140u);
+                                const uint32_t hi = __byte_perm(x, 0x43u, 0x4342u);
+                                o[2 * hw] = bf16x2_eq(lo, key);
+                                o[2 * hw + 1] = bf16x2_eq(hi, key);
                             }
-                            *reinterpret_cast<uint4*>(B + sw128_offset(c, c8)) = make_uint4(o[0], o[1], o[2], o[3]);
+                            *reinterpret_cast<uint4*>(B + sw128_offset(c, 2 * ch + h)) =
+                                make_uint4(o[0], o[1], o[2], o[3]);
                         }
                     }
                 }
                 fence_proxy_async();
-                mbar_arrive(&ready[s]);
+                mbar_arrive(&ready[rb.idx]);
+                mbar_arrive(&lempty[rl.idx]);
+                rb.next(g::NBS);
+                rl.next(NL);
             }
         }
     }
@@ -734,9 +787,9 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     a.ppt = gp.perms_per_tile;
     a.N = (a.ppt * pr.K + 15) / 16 * 16;
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
-    // accumulation length in TMEM between FP64 drains (tuning/testing override)
     a.I0 = I0;
     a.I1 = I1;
+    // accumulation length in TMEM between FP64 drains (tuning/testing override)
     a.drain_kb = g::DRAIN_KB;
     if (const char* env = getenv("PERMANOVA_GEMM_DRAIN")) {
         const int v = atoi(env);

@@ -412,6 +412,16 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
+// Bounded wait by every lane of a warp (each lane acquires the barrier itself,
+// as reading TMEM after a tensor-core commit requires), with an outcome that
+// is the same for all lanes, so warp-synchronous code after it never waits for
+// a lane that gave up.
+__device__ __forceinline__ bool lanes_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                           DevStatus* st, unsigned where, bool obey_abort = true) {
+    const bool ok = wait_bar(bar, parity, abort_flag, st, where, obey_abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
 // Self-test of the bounded wait the kernel above relies on: one thread waits
 // on an mbarrier that nothing arrives on; after `limit` cycles the wait gives
 // up, records DEV_TIMEOUT and the kernel returns normally.
@@ -623,7 +633,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     *reinterpret_cast<uint4*>(lab_rows + p * g::BM + h * g::BK + c16 * 16) = v;
                 }
                 mbar_arrive(epi_bar);
-                if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 10, false)) { ok = false; break; }
+                if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 10, false)) { ok = false; break; }
                 ++epi_phase;
             }
             // this row's selection masks for the unit: bit k of msk[grp] is set when
@@ -660,7 +670,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t c0 = 0; c0 < nkb; c0 += a.drain_kb, ++cc) {
                 const uint32_t b = (uint32_t)(cc & 1);
-                if (!wait_bar(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
+                if (!lanes_wait(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((q4 * 32u) << 16) + b * g::NMAX;
 #pragma unroll
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 #pragma unroll
             for (int grp = 0; grp < g::NMAX / 32; ++grp) acc64[q4 * g::NMAX + 32 * grp + lane] = acc[grp];
             mbar_arrive(epi_bar);
-            if (!wait_bar(epi_bar, epi_phase & 1, abort_flag, st, 11, false)) { ok = false; break; }
+            if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 11, false)) { ok = false; break; }
             ++epi_phase;
             for (uint32_t pp = et; pp < nlab; pp += 128) {
                 double t = 0.0;

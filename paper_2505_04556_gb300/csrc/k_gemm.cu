@@ -33,7 +33,7 @@
 //                (p, g_p(i)) of each row, weight it, reduce over rows;
 //   warps 8-15   build the one-hot B tile (2-stage ring) from the labels, one
 //                B row per thread.
-// Work unit = (band I, tile of up to 64 label rows), band-major so the CTAs
+// Work unit = (band I, tile of up to 128 label rows), band-major so the CTAs
 // running together share a band and read its A tiles from L2.
 // Every wait is bounded; on timeout the kernel records DEV_TIMEOUT, lets the
 // other roles run out, waits for its own copies and MMAs, frees its TMEM and
@@ -50,7 +50,7 @@ namespace g {
 constexpr int BM = 128;             // band height (MMA M)
 constexpr int BK = 64;              // k-block width (one 128-byte swizzle atom of BF16)
 constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
-constexpr int PPT_MAX = 64;         // label rows per tile
+constexpr int PPT_MAX = 128;        // label rows per tile (K = 2 fills N = 256)
 constexpr int NA = 4;               // A-tile stages (bulk copies in flight)
 constexpr int NBS = 2;              // one-hot B-tile stages (built on chip)
 constexpr int DRAIN_KB = 16;        // default k-blocks per accumulator chunk
@@ -65,9 +65,13 @@ constexpr uint32_t OFF_B = NA * A_BYTES;                  // B ring after the A 
 constexpr uint32_t LRING_BYTES = 16384;                   // label ring (ppt x 64 bytes per slot)
 constexpr uint32_t NL_MAX = 16;                           // label slots at most
 constexpr uint32_t OFF_LRING = OFF_B + NBS * B_BYTES;
+// The epilogue's per-unit buffers share one region: the band's row labels
+// (read at the start of a unit) and the four warps' FP64 column sums (written
+// at its end).
 constexpr uint32_t OFF_LABROWS = OFF_LRING + LRING_BYTES;          // [PPT_MAX][BM] uint8
-constexpr uint32_t OFF_ACC64 = OFF_LABROWS + PPT_MAX * BM;         // [4][NMAX] double
-constexpr uint32_t OFF_BAR = OFF_ACC64 + 4 * NMAX * 8;
+constexpr uint32_t OFF_ACC64 = OFF_LABROWS;                        // [4][NMAX] double
+constexpr uint32_t UNIT_BYTES = PPT_MAX * BM > 4 * NMAX * 8 ? PPT_MAX * BM : 4 * NMAX * 8;
+constexpr uint32_t OFF_BAR = OFF_LABROWS + UNIT_BYTES;
 constexpr uint32_t N_BARS = 2 * NA + 2 * NBS + 2 * NL_MAX + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
@@ -454,13 +458,18 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     uint64_t* lempty = lfull + g::NL_MAX;           // [NL_MAX] label slot read by the builders
     uint64_t* acc_full = lempty + g::NL_MAX;        // [2]
     uint64_t* acc_empty = acc_full + 2;             // [2]
-    uint64_t* epi_bar = acc_full + 4;               // epilogue warps meet here twice per unit
+    uint64_t* epi_bar = acc_full + 4;               // epilogue warps meet here 2 or 4 times per unit
     uint64_t* mma_done = acc_full + 5;              // final commit of the MMA thread
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
     uint8_t* lring = sm + g::OFF_LRING;                          // [NL][ppt][64] labels
-    uint8_t* lab_rows = sm + g::OFF_LABROWS;                     // [PPT_MAX][128]
-    double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);  // [4][NMAX]
+    // column sums in the first 8 KB of the per-unit region; the row labels of a
+    // tile of up to 64 label rows fit in the other 8 KB, a larger tile's overlap
+    // the sums and the epilogue then fences the two uses with two more barriers
+    constexpr uint32_t SUM_BYTES = 4 * g::NMAX * 8;
+    const bool overlap = a.ppt * g::BM > g::UNIT_BYTES - SUM_BYTES;
+    uint8_t* lab_rows = sm + g::OFF_LABROWS + (overlap ? 0u : SUM_BYTES);   // [ppt][128]
+    double* acc64 = reinterpret_cast<double*>(sm + g::OFF_ACC64);          // [4][NMAX]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevStatus* st = a.st;
@@ -622,7 +631,14 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
             // the band's row labels for the tile's label rows: k-blocks 2I and 2I+1 of
-            // the tile's label blocks, loaded cooperatively (16 bytes per thread-step)
+            // the tile's label blocks, loaded cooperatively (16 bytes per thread-step);
+            // where they overlap the column sums, only once every thread has read
+            // the previous unit's sums
+            if (overlap) {
+                mbar_arrive(epi_bar);
+                if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 17, false)) { ok = false; break; }
+                ++epi_phase;
+            }
             {
                 const uint8_t* lb = a.labels + ((u % a.n_ptiles) * NB + 2ull * I) * lab_bytes;
                 const uint32_t per_half = a.ppt * (g::BK / 16);
@@ -657,6 +673,12 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     }
                     msk[grp] = m;
                 }
+            }
+            // every thread has its masks before overlapping column sums are written
+            if (overlap) {
+                mbar_arrive(epi_bar);
+                if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 18, false)) { ok = false; break; }
+                ++epi_phase;
             }
             // the group weights of this lane's columns (label row p0 + c/K, group c%K)
             double wc[g::NMAX / 32], acc[g::NMAX / 32];

@@ -145,10 +145,30 @@ def gpu_query_id(torch, dev: int) -> str | None:
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: float) -> dict:
-    """Time the FP64 oracle (Algorithm 1) on the leading n_s x n_s block of
-    the workload with one label row per host thread; n_s is sized so the run
-    takes about ``target_s`` seconds."""
+    """Time the FP64 oracle on the leading n_s x n_s block of the workload:
+    Algorithm 1 on all host threads (the reported value, one label row per
+    thread, the row count sized so the run takes about ``target_s`` seconds),
+    Algorithm 1 on one thread, and Algorithm 2 (tiled, 64 x 64) on all
+    threads, each a bounded sample of label rows."""
     import oracle
     T = oracle.max_threads()
     K = cfg["K"]
@@ -158,23 +178,38 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
     D = synth.recipe_matrix_host(cfg, X[:ns])
     pairs_s = ns * (ns - 1) / 2
 
-    def run(R: int) -> float:
-        rows = np.ascontiguousarray(np.resize(label_rows[:, :ns], (R, ns)).astype(np.int32) % K)
+    def rows_for(R: int) -> np.ndarray:
+        return np.ascontiguousarray(np.resize(label_rows[:, :ns], (R, ns)).astype(np.int32) % K)
+
+    def run(R: int, threads: int, alg: int = 1) -> float:
+        rows = rows_for(R)
         t0 = time.perf_counter()
-        oracle.sW_alg1(D, rows, K, w, threads=T)
+        if alg == 1:
+            oracle.sW_alg1(D, rows, K, w, threads=threads)
+        else:
+            oracle.sW_alg2(D, rows, K, w, 64, threads=threads)
         return time.perf_counter() - t0
 
     R = T
-    t = run(R)
+    t = run(R, T)
     rate = R * pairs_s / max(t, 1e-6)
     if t < target_s / 3:
         R = T * max(1, int(round(target_s * rate / pairs_s / T)))
         R = min(R, 64 * T)
-        t = run(R)
+        t = run(R, T)
         rate = R * pairs_s / t
+    # one thread, a few rows; Algorithm 2 on all threads, one row per thread
+    r1 = max(1, min(8, int(round(target_s / 3 * rate / T / pairs_s))))
+    t1 = run(r1, 1)
+    t2 = run(T, T, alg=2)
     return {"value": rate, "unit": UNIT, "cores": T, "kind": "oracle",
             "sample": f"FP64 Algorithm-1 oracle on the leading {ns}x{ns} block of the workload's "
-                      f"matrix with {R} label rows ({T} threads), {t:.1f} s"}
+                      f"matrix with {R} label rows ({T} threads), {t:.1f} s",
+            "single_thread": {"value": r1 * pairs_s / t1, "sample": f"Algorithm 1, {r1} label rows, "
+                              f"1 thread, {t1:.1f} s"},
+            "alg2_tiled": {"value": T * pairs_s / t2, "sample": f"Algorithm 2 (64 x 64 tiles), {T} "
+                           f"label rows, {T} threads, {t2:.1f} s"},
+            "cpu_model": cpu_model()}
 
 
 # ---------------------------------------------------------------------------

@@ -163,12 +163,13 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: float) -> dict:
+def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: float,
+                extras: bool = True) -> dict:
     """Time the FP64 oracle on the leading n_s x n_s block of the workload:
     Algorithm 1 on all host threads (the reported value, one label row per
     thread, the row count sized so the run takes about ``target_s`` seconds),
     Algorithm 1 on one thread, and Algorithm 2 (tiled, 64 x 64) on all
-    threads, each a bounded sample of label rows."""
+    threads (with ``extras``), each a bounded sample of label rows."""
     import oracle
     T = oracle.max_threads()
     K = cfg["K"]
@@ -198,18 +199,20 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
         R = min(R, 64 * T)
         t = run(R, T)
         rate = R * pairs_s / t
-    # one thread, a few rows; Algorithm 2 on all threads, one row per thread
-    r1 = max(1, min(8, int(round(target_s / 3 * rate / T / pairs_s))))
-    t1 = run(r1, 1)
-    t2 = run(T, T, alg=2)
-    return {"value": rate, "unit": UNIT, "cores": T, "kind": "oracle",
-            "sample": f"FP64 Algorithm-1 oracle on the leading {ns}x{ns} block of the workload's "
-                      f"matrix with {R} label rows ({T} threads), {t:.1f} s",
-            "single_thread": {"value": r1 * pairs_s / t1, "sample": f"Algorithm 1, {r1} label rows, "
-                              f"1 thread, {t1:.1f} s"},
-            "alg2_tiled": {"value": T * pairs_s / t2, "sample": f"Algorithm 2 (64 x 64 tiles), {T} "
-                           f"label rows, {T} threads, {t2:.1f} s"},
-            "cpu_model": cpu_model()}
+    res = {"value": rate, "unit": UNIT, "cores": T, "kind": "oracle", "seconds": t,
+           "sample": f"FP64 Algorithm-1 oracle on the leading {ns}x{ns} block of the workload's "
+                     f"matrix with {R} label rows ({T} threads), {t:.1f} s"}
+    if extras:
+        # one thread, a few rows; Algorithm 2 on all threads, one row per thread
+        r1 = max(1, min(8, int(round(target_s / 3 * rate / T / pairs_s))))
+        t1 = run(r1, 1)
+        t2 = run(T, T, alg=2)
+        res["single_thread"] = {"value": r1 * pairs_s / t1,
+                                "sample": f"Algorithm 1, {r1} label rows, 1 thread, {t1:.1f} s"}
+        res["alg2_tiled"] = {"value": T * pairs_s / t2, "sample": f"Algorithm 2 (64 x 64 tiles), "
+                             f"{T} label rows, {T} threads, {t2:.1f} s"}
+        res["cpu_model"] = cpu_model()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -373,23 +376,27 @@ def main():
         rows = synth.shuffled_rows(cfg["labels"], 64, cfg["seed_perms"])
         per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
         first = oracle_rate(cfg, X, rows, per_step)
-        rates = []
+        rates, secs = [], []
         for k in range(args.steps + args.warmup - 1):
-            r = oracle_rate(cfg, X, rows, per_step)
+            r = oracle_rate(cfg, X, rows, per_step, extras=False)
             if k >= args.warmup - 1:
                 rates.append(r["value"])
+                secs.append(r["seconds"])
         if not rates:
-            rates = [first["value"]]
+            rates, secs = [first["value"]], [first["seconds"]]
         value = statistics.median(rates)
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "n": n, "K": K, "P_total": P,
                            "label_type": cfg["label_type"],
                            "l2": "n/a (CPU)"},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": first["cores"],
-                                 "kind": "oracle", "sample": first["sample"]},
+                                 "kind": "oracle", "sample": first["sample"],
+                                 "single_thread": first.get("single_thread"),
+                                 "alg2_tiled": first.get("alg2_tiled"),
+                                 "cpu_model": first.get("cpu_model")},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)

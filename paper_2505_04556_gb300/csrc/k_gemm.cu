@@ -532,9 +532,17 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
                 for (uint32_t kb = 2 * I; kb < NB; ++kb, ++kc, tile += g::TILE_BYTES) {
-                    // keep the label ring full: slices up to position kc + NL - 1
+                    // label slices: into every slot that is already free, up to position
+                    // kc + NL - 1, and (waiting if need be) up to position kc before A tile
+                    // kc; a slot frees only when the builders are done with it, so waiting
+                    // for one further ahead would hold back the A copies
                     while (lu < n_units && lk < kc + NL) {
-                        if (!wait_bar(&lempty[rl.idx], rl.phase ^ 1, abort_flag, st, 12)) { ok = false; break; }
+                        if (lk > kc) {
+                            if (!mbar_test(&lempty[rl.idx], rl.phase ^ 1)) break;
+                        } else if (!wait_bar(&lempty[rl.idx], rl.phase ^ 1, abort_flag, st, 12)) {
+                            ok = false;
+                            break;
+                        }
                         const uint64_t q = lu % a.n_ptiles;
                         mbar_arrive_expect_tx(&lfull[rl.idx], lab_bytes);
                         bulk_g2s(lring + rl.idx * lab_bytes, a.labels + (q * NB + lkb) * (uint64_t)lab_bytes,

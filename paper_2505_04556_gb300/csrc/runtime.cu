@@ -618,9 +618,8 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     // `stream` (which may still read the arena).  Only the strict upper
     // triangle of D is read by every form, so each 128-row band of rows
     // [128 I, 128 I + 128) is copied from column 128 I on: about half of D.
-    // With the GEMM form the bands go in segments of about equal area that
-    // start on even bands, each with its own event, and segment k's
-    // tensor-core work starts once it has landed.
+    // With the GEMM form the bands go in segments of equal area, each with its
+    // own event, and segment k's tensor-core work starts once it has landed.
     const uint32_t n_bands = (n + 127) / 128;
     const uint32_t n_seg = L.form == PERMANOVA_FORM_GEMM ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
     if (!ctx->copy_stream)
@@ -658,8 +657,7 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
            "copy matrix band");
         acc += band_area(I);
         const size_t k = arr.band.size() - 1;   // segment being filled
-        // segments end on even bands: the tensor-core kernel works on band pairs
-        if (I + 1 == n_bands || ((I + 1) % 2 == 0 && acc >= total * (double)(k + 1) / n_seg)) {
+        if (I + 1 == n_bands || acc >= total * (double)(k + 1) / n_seg) {
             cudaEvent_t e = ctx->copy_events[2 + k];
             CK(cudaEventRecord(e, cs), "record segment");
             arr.seg_ready.push_back(e);

@@ -75,7 +75,9 @@ typedef enum {
  *              indicator columns X_p, on the tcgen05 tensor cores: D^2 split
  *              into BF16 hi + lo, FP32 accumulation in tensor memory, FP64
  *              partial sums.  Needs n_groups <= 256.
- *   AUTO       the planner's choice for (n, K, P). */
+ *   AUTO       the planner's choice for (n, K, P): a bucket timed by
+ *              permanova_autotune if there is one, else GEMM for K <= 36,
+ *              n >= 256 and P >= 32, else PERMBLOCK for P >= 16, else BRUTE. */
 typedef enum {
     PERMANOVA_FORM_AUTO = 0,
     PERMANOVA_FORM_BRUTE = 1,

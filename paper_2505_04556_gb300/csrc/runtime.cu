@@ -36,7 +36,11 @@ struct permanova_ctx {
     int forced_form = PERMANOVA_FORM_AUTO;
     std::map<TuneKey, int> tuned;               // autotuner results
     bool graphs = false;                        // replay captured launch sequences
-    std::map<GraphKey, cudaGraphExec_t> graph_cache;
+    struct CachedGraph {
+        cudaGraphExec_t exec;
+        uint64_t kernels;   // kernels the captured sequence launches (counted on every replay)
+    };
+    std::map<GraphKey, CachedGraph> graph_cache;
     std::mutex mu;
     void* arena = nullptr;
     size_t arena_size = 0;
@@ -182,7 +186,7 @@ int ensure_arena(permanova_ctx* ctx, size_t bytes) {
     size_t want = std::min(ctx->budget, std::max(bytes, ctx->arena_size + ctx->arena_size / 4));
     CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     // captured graphs point into the old arena
-    for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second.exec);
     ctx->graph_cache.clear();
     if (ctx->arena) {
         cudaFree(ctx->arena);
@@ -393,7 +397,7 @@ void permanova_destroy(permanova_ctx* ctx) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         profile_clear(ctx);
-        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second.exec);
         ctx->graph_cache.clear();
         if (ctx->arena) cudaFree(ctx->arena);
         for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
@@ -453,9 +457,12 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
     // replay the launch sequence of an identical earlier call, or capture it now
     const GraphKey key{mat, n, ld, groupings, label_type, K, P, w, out, ctx->arena, L.form, nullptr};
     auto it = ctx->graph_cache.find(key);
+    bool fresh = false;
     if (it == ctx->graph_cache.end()) {
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        const uint64_t before = kernel_launch_count();
         rc = run_sW(ctx, L, pr, w, s);
+        const uint64_t captured = kernel_launch_count() - before;
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(s, &graph);
         if (rc) {
@@ -467,9 +474,12 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        it = ctx->graph_cache.emplace(key, exec).first;
+        it = ctx->graph_cache.emplace(key, permanova_ctx::CachedGraph{exec, captured}).first;
+        fresh = true;
     }
-    CK(cudaGraphLaunch(it->second, s), "cudaGraphLaunch");
+    CK(cudaGraphLaunch(it->second.exec, s), "cudaGraphLaunch");
+    // the capture counted its kernels once (for this first launch); replays count them again
+    if (!fresh) note_launches((unsigned)it->second.kernels);
     return PERMANOVA_OK;
 }
 
@@ -492,7 +502,7 @@ int permanova_set_graphs(permanova_ctx* ctx, int enable) {
     ctx->graphs = enable != 0;
     if (!ctx->graphs) {
         CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second.exec);
         ctx->graph_cache.clear();
     }
     return PERMANOVA_OK;

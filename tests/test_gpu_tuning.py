@@ -54,6 +54,12 @@ def test_graph_replay_matches_direct_launches(ctx):
     direct = torch.empty(P, dtype=torch.float64, device="cuda")
     pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, direct, stream)
     pm.permanova_sync(ctx.handle, stream)
+    # kernels one direct call launches (the counter runs with profiling off)
+    pm.permanova_profile_enable(ctx.handle, False)
+    pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, direct, stream)
+    pm.permanova_sync(ctx.handle, stream)
+    per_call = pm.permanova_profile_read(ctx.handle)["kernel_launches"]
+    assert per_call >= 2
     pm.permanova_set_graphs(ctx.handle, True)
     try:
         out = torch.empty(P, dtype=torch.float64, device="cuda")
@@ -62,6 +68,8 @@ def test_graph_replay_matches_direct_launches(ctx):
             pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, out, stream)
             pm.permanova_sync(ctx.handle, stream)
             assert torch.equal(out, direct)
+        # replayed kernels are counted like launched ones
+        assert pm.permanova_profile_read(ctx.handle)["kernel_launches"] == 3 * per_call
         # replays read the buffers at run time: new labels in the same buffer
         rows2 = synth.shuffled_rows(rows[0], P, 99)
         with torch.cuda.stream(stream):

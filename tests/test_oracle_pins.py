@@ -58,6 +58,51 @@ def test_alg1_equals_exact_groupwise_pair_sum(n, K, seed):
     assert abs(got - float(exact)) <= 1e-13 * max(1.0, abs(float(exact)))
 
 
+@pytest.mark.parametrize("n,K,P,seed", [(40, 1, 3, 1), (57, 3, 5, 2), (130, 10, 4, 3)])
+def test_alg1_equals_one_hot_contraction(n, K, P, seed):
+    """The tensor-core form's algebra, written out in FP64 with numpy: with M
+    the strict upper triangle of D o D and X_p the one-hot (n x K) indicator
+    of row p, Z_p = M X_p and s_W[p] = sum_i w[g_p(i)] Z_p[i, g_p(i)]."""
+    D, lab = _random_case(n, K, seed)
+    rng = np.random.default_rng(seed + 7)
+    rows = np.stack([rng.permutation(lab) for _ in range(P)]).astype(np.int32)
+    w = rng.uniform(0.1, 2.0, size=K)
+    M = np.triu(D.astype(np.float64) ** 2, k=1)
+    ref = []
+    for g in rows:
+        X = np.zeros((n, K))
+        X[np.arange(n), g] = 1.0
+        Z = M @ X
+        ref.append(float(np.sum(w[g] * Z[np.arange(n), g])))
+    got = oracle.sW_alg1(D, rows, K, w)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def _bf16_rne(x):
+    """float32 -> the nearest bfloat16 (ties to even), returned as float32:
+    keep the top 16 bits of the rounded bit pattern."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_hi_lo_split_error_bound():
+    """The GEMM form stores d^2 (FP32) as hi = bf16(d^2) and lo = bf16(d^2 - hi)
+    (the difference is exact in FP32): hi + lo carries 16 significant bits, so
+    |hi + lo - d^2| <= 2^-17 |d^2| for every normal value.  Checked on a log-
+    uniform spread of magnitudes and on d^2 of random distances."""
+    rng = np.random.default_rng(11)
+    v = np.concatenate([np.exp(rng.uniform(-60.0, 60.0, 200000)),
+                        (rng.uniform(0.0, 3.0, 200000) ** 2)]).astype(np.float32)
+    v = v[v > np.float32(1e-30)]
+    hi = _bf16_rne(v)
+    lo = _bf16_rne((v - hi).astype(np.float32))   # exact difference in FP32
+    err = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - v.astype(np.float64))
+    assert np.all(err <= 2.0 ** -17 * v.astype(np.float64))
+    # and the bound is nearly reached: 16 bits, not more
+    assert np.max(err / v.astype(np.float64)) > 2.0 ** -19
+
+
 def test_alg1_exact_on_integer_matrix_power_of_two_groups():
     # integer d in [0, 15], groups of 8/4/4 -> every partial sum is exact in FP64
     n = 16

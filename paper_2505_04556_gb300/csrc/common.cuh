@@ -150,8 +150,6 @@ struct TestScalars {
     unsigned long long n_ge;
     unsigned long long n_perms;
 };
-cudaError_t launch_finalize(const double* sW, uint64_t n_perms, const double* sT_sum, uint32_t n,
-                            uint32_t K, TestScalars* out, cudaStream_t s);
 // n_tests tests in one pass: sW and out hold n_tests segments / results
 cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
                                   const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,

@@ -282,12 +282,6 @@ __global__ void k_finalize(const double* __restrict__ sW_all, uint64_t n_perms,
     }
 }
 
-cudaError_t launch_finalize(const double* sW, uint64_t n_perms, const double* sT_sum, uint32_t n,
-                            uint32_t K, TestScalars* out, cudaStream_t s) {
-    k_finalize<<<1, 1024, 0, s>>>(sW, n_perms, sT_sum, n, K, out);
-    return launched(1);
-}
-
 cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
                                   const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,
                                   cudaStream_t s) {

@@ -13,7 +13,7 @@
 // hi + lo carries 16 significant bits (relative error <= 2^-17 per term); the
 // one-hot operand is exact in BF16.  Both planes multiply the same B operand
 // into one FP32 accumulator in tensor memory.  The accumulator is drained
-// every drain_kb k-blocks (default 16 = 1,024 columns); the drained row values are
+// every drain_kb k-blocks (default 32 = 2,048 columns); the drained row values are
 // weighted in FP64, reduced over the 128 rows in a fixed order and
 // accumulated in FP64.
 //
@@ -53,7 +53,7 @@ constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
 constexpr int PPT_MAX = 128;        // label rows per tile (K = 2 fills N = 256)
 constexpr int NA = 4;               // A-tile stages (bulk copies in flight)
 constexpr int NBS = 2;              // one-hot B-tile stages (built on chip)
-constexpr int DRAIN_KB = 16;        // default k-blocks per accumulator chunk
+constexpr int DRAIN_KB = 32;        // default k-blocks per accumulator chunk
 constexpr int PREFETCH_KB = 8;      // L2 prefetch distance along the band (k-blocks)
 constexpr int THREADS = 512;        // 16 warps
 constexpr int BUILDERS = 256;       // warps 8-15: one B row per thread

@@ -501,14 +501,21 @@ def main():
 
         e2e_step()
         barrier()
+        e2e_sampler = ClockSampler(gpu_query_id(torch, dev))
+        e2e_sampler.start()
         t0 = time.perf_counter()
+        step_ms = []
         for _ in range(args.e2e_steps):
+            ts = time.perf_counter()
             e2e_step()
+            step_ms.append(round(1e3 * (time.perf_counter() - ts), 2))
         barrier()
         te, rows_e2e = combine_ranks(time.perf_counter() - t0, float(B * args.e2e_steps))
+        e2e_clocks = e2e_sampler.stop()
         e2e = {"value": pairs * rows_e2e / te, "unit": UNIT,
                "h2d_bytes_per_step": int(host_matrix_bytes(n) + B * n + K * 4),
-               "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps,
+               "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps, "step_ms": step_ms,
+               "clocks": e2e_clocks,
                "api": "permanova_sW_host (pinned host D, labels, weights, results; "
                       "copies D's band trapezoids in segments overlapped with the kernels)"}
 

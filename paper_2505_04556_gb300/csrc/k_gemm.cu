@@ -8,20 +8,26 @@
 // (label row, group).  This costs K times the useful work of the brute force
 // but runs on the tensor cores.
 //
-// Precision.  d^2 is formed in FP32 and split into two BF16 planes,
-// hi = bf16(d^2), lo = bf16(d^2 - hi) (the difference is exact in FP32), so
-// hi + lo carries 16 significant bits (relative error <= 2^-17 per term); the
-// one-hot operand is exact in BF16.  Both planes multiply the same B operand
-// into one FP32 accumulator in tensor memory.  The accumulator is drained
-// every drain_kb k-blocks (default 32 = 2,048 columns); the drained row values are
-// weighted in FP64, reduced over the 128 rows in a fixed order and
-// accumulated in FP64.
+// Precision.  d^2 is formed in FP32 and scaled by a power of two S_I per
+// 128-row band (S_I x_max < 2^24, x_max the band's largest d^2, found by a
+// pass over the band before the split), y = S_I d^2, then split into
+//     h = bf16(y),   hi plane = bf16(2^7 h)  (exact),   lo plane = fp16(y - h)
+// (y - h is exact in FP32 and |y - h| <= 2^-8 y fits FP16), so hi + lo
+// carries 19 significant bits: relative error <= 2^-20 per term, or an
+// absolute 2^-25 / S_I (about 2^-48 x_max) where y - h is an FP16 subnormal.
+// The one-hot operand holds 0x3C00 where a label matches: FP16 1.0, and as
+// BF16 exactly 2^-7, so one B tile serves both planes: the hi MMA (BF16 A and
+// B) adds 2^7 h * 2^-7 = h, the lo MMA (FP16 A and B) adds y - h, into one
+// FP32 accumulator in tensor memory.  The accumulator is drained every
+// drain_kb k-blocks; the drained row values are weighted by w_g / S_I in
+// FP64, reduced over the 128 rows in a fixed order and accumulated in FP64.
 //
 // Layout.  A prep kernel writes, for every 128-row band I and 64-column
 // k-block kb >= 2I of the triangle, one 32 KB tile: the hi plane (128 x 64
-// BF16) then the lo plane, each already in the tensor core's K-major 128-byte
-// swizzled layout, so one bulk copy (TMA engine) moves both planes.  Entries
-// with j <= i, i >= n or j >= n are zero.
+// BF16) then the lo plane (128 x 64 FP16), each already in the tensor core's
+// K-major 128-byte swizzled layout, so one bulk copy (TMA engine) moves both
+// planes.  Entries with j <= i, i >= n or j >= n are zero.  After the tiles,
+// one 32-bit word per band holds the bit pattern of the band's largest d^2.
 //
 // Kernel.  Persistent, one CTA per SM, 16 warps:
 //   warp 0       bulk-copies the A tiles into a 4-stage ring and the 64-column
@@ -41,6 +47,7 @@
 #include "common.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdlib>
 
@@ -53,7 +60,7 @@ constexpr int NMAX = 256;           // MMA N (accumulator columns per buffer)
 constexpr int PPT_MAX = 128;        // label rows per tile (K = 2 fills N = 256)
 constexpr int NA = 4;               // A-tile stages (bulk copies in flight)
 constexpr int NBS = 2;              // one-hot B-tile stages (built on chip)
-constexpr int DRAIN_KB = 32;        // default k-blocks per accumulator chunk
+constexpr int DRAIN_KB = 8;         // default k-blocks per accumulator chunk
 constexpr int PREFETCH_KB = 8;      // L2 prefetch distance along the band (k-blocks)
 constexpr int THREADS = 512;        // 16 warps
 constexpr int BUILDERS = 256;       // warps 8-15: one B row per thread
@@ -140,7 +147,7 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -185,11 +192,11 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], uint32_t lane)
     return v[0];
 }
 
-// Packed BF16 equality: each 16-bit half of the result is 1.0 (0x3F80) where
-// the halves of a and b are equal values, else 0.0.
-__device__ __forceinline__ uint32_t bf16x2_eq(uint32_t a, uint32_t b) {
+// Packed FP16 equality: each 16-bit half of the result is FP16 1.0 (0x3C00)
+// where the halves of a and b are equal values, else 0.0.
+__device__ __forceinline__ uint32_t f16x2_eq(uint32_t a, uint32_t b) {
     uint32_t d;
-    asm("set.eq.bf16x2.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    asm("set.eq.f16x2.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
 
@@ -205,9 +212,24 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major.
+// Instruction descriptors: kind::f16 with BF16 (or FP16) A and B, FP32 D,
+// both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t M, uint32_t N) {
+    return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Band scale S = 2^s from the bit pattern of the band's largest d^2 (a
+// non-negative float, or 0): S x_max lies in [2^23, 2^24); zero, infinite or
+// NaN maxima give S = 1, and s is clamped to [-100, 100].
+__host__ __device__ __forceinline__ int band_scale_exp(uint32_t max_bits) {
+    const int ef = (int)((max_bits >> 23) & 0xFFu);
+    if (max_bits == 0u || ef == 0xFF) return 0;
+    const int e = ef == 0 ? -126 : ef - 127;
+    const int s = 23 - e;
+    return s > 100 ? 100 : (s < -100 ? -100 : s);
 }
 
 // Byte offset of 16-byte chunk c (0..7) of row r inside a K-major 128-byte
@@ -239,59 +261,112 @@ static __host__ __device__ __forceinline__ uint64_t tiles_before_band(uint64_t I
     return I * NB - I * (I - 1);
 }
 
-size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
+static size_t tile_bytes_total(const GemmPlan& gp) {
     const uint64_t nb = gp.n_bands;
     return (size_t)(nb * (nb + 1)) * g::TILE_BYTES;
 }
 
+size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
+    return tile_bytes_total(gp) + (size_t)gp.n_bands * sizeof(uint32_t);
+}
+
 // ---------------------------------------------------------------------------
-// operand preparation: D -> swizzled BF16 hi/lo tiles of the strict upper triangle
+// operand preparation: D -> per-band scale, then swizzled hi (BF16) / lo (FP16)
+// tiles of the strict upper triangle
 // ---------------------------------------------------------------------------
+// Tile t of bands [I0, I1): its band I and k-block kb.
+__device__ __forceinline__ void tile_coords(uint64_t t, uint32_t n_bands, uint32_t& I, uint32_t& kb) {
+    const uint64_t NB = 2ull * n_bands;
+    uint32_t lo = 0, hi = n_bands - 1;   // largest I with tiles_before_band(I) <= t
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (tiles_before_band(mid, NB) <= t) lo = mid; else hi = mid - 1;
+    }
+    I = lo;
+    kb = (uint32_t)(t - tiles_before_band(I, NB)) + 2 * I;
+}
+
+// d^2 of the 8 entries (i, j0 .. j0+7) in FP32, zero outside the strict upper
+// triangle (j <= i, i >= n or j >= n).
+__device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t n, uint64_t ld, bool vec,
+                                         bool diag, uint32_t i, uint32_t j0, float (&x)[8]) {
+    float v[8];
+    if (i < n && vec && !diag && j0 + 7 < n) {
+        const float4* src = reinterpret_cast<const float4*>(mat + (uint64_t)i * ld + j0);
+        const float4 a = __ldg(src), b = __ldg(src + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t j = j0 + e;
+            v[e] = 0.f;
+            if (i < n && j < n && j > i) v[e] = __ldg(mat + (uint64_t)i * ld + j);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t j = j0 + e;
+        x[e] = (i < n && j < n && j > i) ? v[e] * v[e] : 0.f;
+    }
+}
+
+// Largest d^2 of each band, as the bit pattern of a non-negative float
+// (bit order = value order), into bmax[I] (zeroed beforehand).
+__global__ void __launch_bounds__(256)
+k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
+                uint64_t t0, uint64_t t1, uint32_t* __restrict__ bmax) {
+    __shared__ uint32_t wmax[8];
+    for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+        uint32_t I, kb;
+        tile_coords(t, n_bands, I, kb);
+        const bool diag = kb < 2 * I + 2;
+        uint32_t m = 0;
+        for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
+            float x[8];
+            squared8(mat, n, ld, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) m = max(m, __float_as_uint(x[e]));
+        }
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t b = wmax[0];
+#pragma unroll
+            for (int w = 1; w < 8; ++w) b = max(b, wmax[w]);
+            if (b) atomicMax(bmax + I, b);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
-            uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles) {
-    const uint64_t NB = 2ull * n_bands;
+            uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles, const uint32_t* __restrict__ bmax) {
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
-        // band I: largest I with tiles_before_band(I) <= t
-        uint32_t lo = 0, hi = n_bands - 1;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi + 1) / 2;
-            if (tiles_before_band(mid, NB) <= t) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t I = lo;
-        const uint32_t kb = (uint32_t)(t - tiles_before_band(I, NB)) + 2 * I;
+        uint32_t I, kb;
+        tile_coords(t, n_bands, I, kb);
+        const float S = __uint_as_float((uint32_t)(127 + band_scale_exp(bmax[I])) << 23);
         uint8_t* tile = tiles + t * g::TILE_BYTES;
         const bool diag = kb < 2 * I + 2;
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             const uint32_t r = job >> 3, c8 = job & 7;
-            const uint32_t i = I * g::BM + r;
-            const uint32_t j0 = kb * g::BK + c8 * 8;
-            float v[8];
-            if (i < n && vec && !diag && j0 + 7 < n) {
-                const float4* src = reinterpret_cast<const float4*>(mat + (uint64_t)i * ld + j0);
-                const float4 a = __ldg(src), b = __ldg(src + 1);
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t j = j0 + e;
-                    v[e] = 0.f;
-                    if (i < n && j < n && j > i) v[e] = __ldg(mat + (uint64_t)i * ld + j);
-                }
-            }
+            float x[8];
+            squared8(mat, n, ld, vec, diag, I * g::BM + r, kb * g::BK + c8 * 8, x);
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
-                const uint32_t j = j0 + e;
-                // strict upper triangle only: anything else contributes exactly zero
-                const float d0 = (i < n && j < n && j > i) ? v[e] * v[e] : 0.f;
-                const float d1 = (i < n && j + 1 < n && j + 1 > i) ? v[e + 1] * v[e + 1] : 0.f;
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(d0), h1 = __float2bfloat16_rn(d1);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(d0 - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(d1 - __bfloat162float(h1));
-                hw[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                lw[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                uint16_t hb[2], lb[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float y = S * x[e + q];                    // exact: a power of two
+                    const float h = __bfloat162float(__float2bfloat16_rn(y));
+                    hb[q] = __bfloat16_as_ushort(__float2bfloat16_rn(h * 128.f));   // exact
+                    lb[q] = __half_as_ushort(__float2half_rn(y - h));             // y - h exact
+                }
+                hw[e / 2] = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16);
+                lw[e / 2] = (uint32_t)lb[0] | ((uint32_t)lb[1] << 16);
             }
             const uint32_t off = sw128_offset(r, c8);
             *reinterpret_cast<uint4*>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -309,8 +384,13 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
     const uint64_t t0 = tiles_before_band(I0, NB), t1 = tiles_before_band(I1, NB);
     const uint64_t n_tiles = t1 - t0;
     const unsigned blocks = (unsigned)(n_tiles < 152ull * 16 ? n_tiles : 152ull * 16);
-    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, (uint8_t*)scratch);
-    return launched(1);
+    uint8_t* tiles = (uint8_t*)scratch;
+    uint32_t* bmax = reinterpret_cast<uint32_t*>(tiles + tile_bytes_total(gp));
+    cudaError_t e = cudaMemsetAsync(bmax + I0, 0, (size_t)(I1 - I0) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, bmax);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, tiles, bmax);
+    return launched(2);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,6 +462,7 @@ struct Ring {
 
 struct GemmArgs {
     const uint8_t* tiles;      // prepared A tiles
+    const uint32_t* bmax;      // per band: bit pattern of the largest d^2 (sets S_I)
     const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
     const double* w;
     uint64_t w_set_rows;       // label rows per weight set (0: one set)
@@ -576,7 +657,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(g::BM, a.N);
+            const uint32_t idesc_hi = idesc_bf16(g::BM, a.N), idesc_lo = idesc_f16(g::BM, a.N);
             uint64_t cc = 0;
             Ring ra, rb;
             bool ok = true;
@@ -604,8 +685,8 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 #pragma unroll
                         for (int kk = 0; kk < g::BK / 16; ++kk) {
                             const uint64_t bd = sw128_desc(sb + kk * 32);
-                            mma_bf16(d_tmem, sw128_desc(sa + kk * 32), bd, idesc, (k > c0 || kk > 0) ? 1u : 0u);
-                            mma_bf16(d_tmem, sw128_desc(sa + g::PLANE_BYTES + kk * 32), bd, idesc, 1u);
+                            mma_f16(d_tmem, sw128_desc(sa + kk * 32), bd, idesc_hi, (k > c0 || kk > 0) ? 1u : 0u);
+                            mma_f16(d_tmem, sw128_desc(sa + g::PLANE_BYTES + kk * 32), bd, idesc_lo, 1u);
                         }
                         mma_commit(&aempty[ra.idx]);
                         mma_commit(&bempty[rb.idx]);
@@ -688,13 +769,15 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 18, false)) { ok = false; break; }
                 ++epi_phase;
             }
-            // the group weights of this lane's columns (label row p0 + c/K, group c%K)
+            // the group weights of this lane's columns (label row p0 + c/K, group c%K),
+            // divided by the band's scale S_I (a power of two: exact)
+            const double inv_s = __longlong_as_double((long long)(1023 - band_scale_exp(a.bmax[I])) << 52);
             double wc[g::NMAX / 32], acc[g::NMAX / 32];
 #pragma unroll
             for (int grp = 0; grp < g::NMAX / 32; ++grp) {
                 const uint32_t c = 32u * grp + lane;
                 wc[grp] = (c < used && c / K < nlab)
-                              ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) : 0.0;
+                              ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) * inv_s : 0.0;
                 acc[grp] = 0.0;
             }
             const uint32_t nkb = NB - 2 * I;
@@ -740,9 +823,10 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         // ------------------------------------------------------------ B builders
         // Thread t builds row t of every B tile (the one-hot column of label row
         // t / K and group t % K over the k-block's 64 objects).  A label byte L
-        // becomes the BF16 bit pattern 0x43LL (a distinct finite value for each
+        // becomes the FP16 bit pattern 0x43LL (a distinct finite value for each
         // of the 256 byte values) by one byte permute per two labels, and one
-        // packed BF16 equality compare against 0x43gg writes 1.0 or 0.0 for both.
+        // packed FP16 equality compare against 0x43gg writes 0x3C00 (FP16 1.0,
+        // BF16 2^-7) or 0 for both.
         const uint32_t c = threadIdx.x - 256;      // 0..255
         const uint32_t K = a.K;
         const uint32_t rows_used = a.ppt * K;
@@ -777,11 +861,11 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 #pragma unroll
                             for (int hw = 0; hw < 2; ++hw) {
                                 const uint32_t x = xs[2 * h + hw];
-                                // labels 0,1 and 2,3 of x as BF16 pairs (0x43L0, 0x43L1), (0x43L2, 0x43L3)
+                                // labels 0,1 and 2,3 of x as FP16 pairs (0x43L0, 0x43L1), (0x43L2, 0x43L3)
                                 const uint32_t lo = __byte_perm(x, 0x43u, 0x4140u);
                                 const uint32_t hi = __byte_perm(x, 0x43u, 0x4342u);
-                                o[2 * hw] = bf16x2_eq(lo, key);
-                                o[2 * hw + 1] = bf16x2_eq(hi, key);
+                                o[2 * hw] = f16x2_eq(lo, key);
+                                o[2 * hw + 1] = f16x2_eq(hi, key);
                             }
                             *reinterpret_cast<uint4*>(B + sw128_offset(c, 2 * ch + h)) =
                                 make_uint4(o[0], o[1], o[2], o[3]);
@@ -814,6 +898,7 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     if (I0 >= I1) return cudaSuccess;
     GemmArgs a;
     a.tiles = (const uint8_t*)scratch;
+    a.bmax = reinterpret_cast<const uint32_t*>(a.tiles + tile_bytes_total(gp));
     a.labels = (const uint8_t*)pr.labels;
     a.w = pr.w;
     a.w_set_rows = pr.w_set_rows;

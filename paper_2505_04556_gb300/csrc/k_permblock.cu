@@ -13,8 +13,13 @@
 //     selectors feed one packed FP32x2 FMA (2 evaluations per FFMA2);
 //   * D^2 is read from shared memory with 128-bit broadcast loads;
 //   * as in Algorithm 2, the row segment is summed unweighted and multiplied
-//     by w_{g_p(i)} once.  Row segments (64 terms, four FP32 partial sums)
-//     are weighted and accumulated in FP64 (one DFMA per 64 evaluations);
+//     by w_{g_p(i)} once.  Each thread converts its 64 row weights to FP32
+//     once per CTA (shared memory); a row segment (64 terms, four FP32
+//     partial sums) is weighted with one FP32 FMA into a group sum of 8
+//     rows, and each group sum is added to an FP64 total, so the slow FP64
+//     pipe sees two operations per 512 evaluations.  Worst-case relative
+//     error of a group: about 28 unit roundoffs (16-term chains, the partial
+//     reduction, the weight's rounding and product, the 8-row chain), 1.7e-6;
 //     the next row's label is fetched one row ahead; the CTA writes one FP64
 //     partial per (band, label row).
 // Labels arrive as uint8 (K <= 256) or uint16 codes whose row stride is a
@@ -26,6 +31,7 @@ namespace pmn {
 
 constexpr int PB_P = 128;  // label rows per CTA (one per thread)
 constexpr int PB_T = 64;   // band height and column-tile width
+constexpr int PB_G = 8;    // rows per FP32 group sum
 
 __device__ __forceinline__ float code_u8(uint32_t word, int k) {
     // bytes: [label byte k, 0, 0, 0x4B] -> float 2^23 + label
@@ -83,6 +89,7 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
                uint32_t K,
                uint32_t n_pblocks, double* __restrict__ partials, const DevStatus* __restrict__ st) {
     __shared__ __align__(16) float d2[PB_T][PB_T];
+    __shared__ float wrow[PB_T][PB_P];  // this thread's row weights, FP32
     const uint32_t band = blockIdx.x / n_pblocks;
     const uint32_t q = blockIdx.x % n_pblocks;
     const uint64_t p = (uint64_t)q * PB_P + threadIdx.x;
@@ -97,6 +104,8 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     const uint32_t r0 = band * PB_T;
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     double total = 0.0;
+    for (uint32_t r = 0; r < rows; ++r)
+        wrow[r][threadIdx.x] = (float)__ldg(w + min((uint32_t)g[r0 + r], K - 1));
 
     for (uint32_t j0 = r0; j0 < n; j0 += PB_T) {
         __syncthreads();  // the previous tile has been consumed
@@ -134,24 +143,29 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
         __syncthreads();
 
         uint32_t gnext = min((uint32_t)g[r0], K - 1);
-        for (uint32_t r = 0; r < rows; ++r) {
-            const uint32_t gi = gnext;
-            if (r + 1 < rows) gnext = min((uint32_t)g[r0 + r + 1], K - 1);   // prefetch
-            const float fgi = code_of(gi);
-            const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
-            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        for (uint32_t rg = 0; rg < rows; rg += PB_G) {
+            const uint32_t rend = min(rg + PB_G, rows);
+            float group = 0.f;
+            for (uint32_t r = rg; r < rend; ++r) {
+                const uint32_t gi = gnext;
+                if (r + 1 < rows) gnext = min((uint32_t)g[r0 + r + 1], K - 1);   // prefetch
+                const float fgi = code_of(gi);
+                const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
+                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c4 = 0; c4 < PB_T / 4; ++c4) {
-                const float4 dv = drow[c4];
-                const float e0 = select_eq(cl[4 * c4 + 0], fgi);
-                const float e1 = select_eq(cl[4 * c4 + 1], fgi);
-                const float e2 = select_eq(cl[4 * c4 + 2], fgi);
-                const float e3 = select_eq(cl[4 * c4 + 3], fgi);
-                a0 = __ffma2_rn(make_float2(e0, e1), make_float2(dv.x, dv.y), a0);
-                a1 = __ffma2_rn(make_float2(e2, e3), make_float2(dv.z, dv.w), a1);
+                for (int c4 = 0; c4 < PB_T / 4; ++c4) {
+                    const float4 dv = drow[c4];
+                    const float e0 = select_eq(cl[4 * c4 + 0], fgi);
+                    const float e1 = select_eq(cl[4 * c4 + 1], fgi);
+                    const float e2 = select_eq(cl[4 * c4 + 2], fgi);
+                    const float e3 = select_eq(cl[4 * c4 + 3], fgi);
+                    a0 = __ffma2_rn(make_float2(e0, e1), make_float2(dv.x, dv.y), a0);
+                    a1 = __ffma2_rn(make_float2(e2, e3), make_float2(dv.z, dv.w), a1);
+                }
+                // weight applied once per row segment (Algorithm 2)
+                group = fmaf((a0.x + a0.y) + (a1.x + a1.y), wrow[r][threadIdx.x], group);
             }
-            // weight applied once per row segment (Algorithm 2), accumulated in FP64
-            total = fma((double)((a0.x + a0.y) + (a1.x + a1.y)), __ldg(w + gi), total);
+            total += (double)group;
         }
     }
     if (active) partials[(uint64_t)band * P + p] = total;

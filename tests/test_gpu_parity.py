@@ -168,6 +168,29 @@ def test_single_group_closed_form(ctx):
         np.testing.assert_allclose(got, st, rtol=RTOL)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n,K", [(3000, 3), (2051, 1)])
+@pytest.mark.parametrize("c", [0.7937, 1.0019550323486328, 2.989486])
+def test_constant_matrix_closed_form(ctx, form, n, K, c):
+    """Every term equal is the worst case for accumulation order: each FP32
+    rounding (and the tensor core's truncating accumulation) errs the same way.
+    For d_ij = c off the diagonal, s_W[p] = c^2 sum_g w_g n_g (n_g - 1) / 2,
+    evaluated in FP64 from the label counts (Sec. 1's definition of s_W).
+    c = 1.0019550323486328 squares to 1 + 2^-8 + 2^-17, the worst value for a
+    split of d^2 into two BF16 halves; c = 2.989486 was the worst constant for
+    the tensor-core accumulation in a sweep of 60 values."""
+    c = np.float32(c)
+    D = np.full((n, n), c, dtype=np.float32)
+    np.fill_diagonal(D, 0.0)
+    rng = np.random.default_rng(77)
+    rows = np.stack([rng.permutation(np.arange(n) % K) for _ in range(40)]).astype(np.int32)
+    sizes = np.bincount(rows[0], minlength=K)
+    w = (1.0 / sizes).astype(np.float32)
+    want = float(c) ** 2 * sum(float(w[g]) * sizes[g] * (sizes[g] - 1) / 2 for g in range(K))
+    got = _run_sW(ctx, D, rows, K, w, form)
+    np.testing.assert_allclose(got, np.full(rows.shape[0], want), rtol=RTOL)
+
+
 def test_permutations_bit_exact_with_oracle(ctx):
     obs = synth.observed_labels([37, 20, 13, 3], 12)
     n = obs.size

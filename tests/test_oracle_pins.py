@@ -86,21 +86,54 @@ def _bf16_rne(x):
     return b.astype(np.uint32).view(np.float32)
 
 
-def test_bf16_hi_lo_split_error_bound():
-    """The GEMM form stores d^2 (FP32) as hi = bf16(d^2) and lo = bf16(d^2 - hi)
-    (the difference is exact in FP32): hi + lo carries 16 significant bits, so
-    |hi + lo - d^2| <= 2^-17 |d^2| for every normal value.  Checked on a log-
-    uniform spread of magnitudes and on d^2 of random distances."""
+def _band_scale(x_max):
+    """Power of two S with S * x_max in [2^23, 2^24) (S = 1 for a zero maximum)."""
+    if x_max == 0.0:
+        return 1.0
+    e = int(np.floor(np.log2(np.float64(x_max))))
+    return 2.0 ** min(100, max(-100, 23 - e))
+
+
+def _split(x, S):
+    """The GEMM form's split of d^2 = x (FP32) in a band with scale S:
+    y = S x, h = bf16(y), hi plane = bf16(2^7 h), lo plane = fp16(y - h)."""
+    y = (np.float32(S) * x).astype(np.float32)
+    h = _bf16_rne(y)
+    hi = _bf16_rne((h * np.float32(128.0)).astype(np.float32))
+    lo = (y - h).astype(np.float32).astype(np.float16)
+    return y, h, hi, lo
+
+
+def test_gemm_split_error_bound():
+    """hi (BF16) + lo (FP16) carry 19 significant bits of S x: |hi/2^7 + lo - S x|
+    <= max(2^-20 S x, 2^-25) (2^-25 = half the FP16 subnormal spacing), the hi
+    plane is exactly 2^7 bf16(S x), and the lo plane never overflows FP16.
+    Checked per band on log-uniform magnitudes, random distances, and the
+    value 1 + 2^-8 + 2^-17 that is the worst case of a BF16 + BF16 split."""
     rng = np.random.default_rng(11)
-    v = np.concatenate([np.exp(rng.uniform(-60.0, 60.0, 200000)),
-                        (rng.uniform(0.0, 3.0, 200000) ** 2)]).astype(np.float32)
-    v = v[v > np.float32(1e-30)]
-    hi = _bf16_rne(v)
-    lo = _bf16_rne((v - hi).astype(np.float32))   # exact difference in FP32
-    err = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - v.astype(np.float64))
-    assert np.all(err <= 2.0 ** -17 * v.astype(np.float64))
-    # and the bound is nearly reached: 16 bits, not more
-    assert np.max(err / v.astype(np.float64)) > 2.0 ** -19
+    bands = [np.exp(rng.uniform(-30.0, 30.0, 100000)),
+             rng.uniform(0.0, 3.0, 100000) ** 2,
+             np.exp(rng.uniform(-8.0, 8.0, 100000)) * 1e6,
+             np.full(1000, 1 + 2.0 ** -8 + 2.0 ** -17)]
+    worst = 0.0
+    for v in bands:
+        x = v.astype(np.float32)
+        S = _band_scale(float(x.max()))
+        assert 2.0 ** 23 <= S * float(x.max()) < 2.0 ** 24
+        y, h, hi, lo = _split(x, S)
+        assert np.array_equal(hi.astype(np.float64), 128.0 * h.astype(np.float64))
+        assert np.all(np.isfinite(lo)) and np.max(np.abs(lo.astype(np.float64))) <= 2.0 ** 15
+        got = h.astype(np.float64) + lo.astype(np.float64)
+        err = np.abs(got - y.astype(np.float64))
+        assert np.all(err <= np.maximum(2.0 ** -20 * y.astype(np.float64), 2.0 ** -25))
+        normal = np.abs((y - h).astype(np.float64)) >= 2.0 ** -14
+        worst = max(worst, float(np.max(err[normal] / y.astype(np.float64)[normal])))
+    # 19 bits, not more: the bound is nearly reached
+    assert worst > 2.0 ** -22
+    # the old BF16 + BF16 worst case is now far inside the bound
+    x = np.float32(1 + 2.0 ** -8 + 2.0 ** -17)
+    lo16 = _bf16_rne((x - _bf16_rne(x)).astype(np.float32))
+    assert abs(float(_bf16_rne(x)) + float(lo16) - float(x)) / float(x) > 2.0 ** -18
 
 
 def test_alg1_exact_on_integer_matrix_power_of_two_groups():

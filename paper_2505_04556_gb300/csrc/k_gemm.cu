@@ -35,8 +35,9 @@
 //                runs up to 16 k-blocks ahead;
 //   warp 1       owns 512 TMEM columns (two 128 x 256 FP32 accumulators) and
 //                issues the tcgen05.mma instructions (one thread);
-//   warps 4-7    drain the accumulators (tcgen05.ld), keep column
-//                (p, g_p(i)) of each row, weight it, reduce over rows;
+//   warps 4-7    drain the accumulators (tcgen05.ld, four rows of a column per
+//                thread), keep column (p, g_p(i)) of each row, reduce over rows,
+//                weight each column once per unit;
 //   warps 8-15   build the one-hot B tile (2-stage ring) from the labels, one
 //                B row per thread.
 // Work unit = (band I, tile of up to 128 label rows), band-major so the CTAs
@@ -116,6 +117,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// The same test, but a thread whose phase has not completed sleeps until it
+// completes or about 20 microseconds pass (the suspend-time hint), instead of
+// returning at once: waiting warps take no issue slots while they wait.
+__device__ __forceinline__ bool mbar_sleep(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -160,15 +173,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                      smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 lanes x 128 bits, 8 times along the columns: register 2 m holds (lane
+// base + lane / 4, column 4 m + lane % 4), register 2 m + 1 the same column 8
+// lanes further down.
+__device__ __forceinline__ void tmem_ld16x128_x8(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.16x128b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[15])
         : "r"(taddr)
         : "memory");
 }
@@ -176,17 +190,27 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Butterfly reduce-scatter: lane l returns sum over the warp's 32 lanes of
-// v[l].  Five exchange steps (16, 8, 4, 2, 1 values), a fixed summation tree.
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], uint32_t lane) {
+// acc += x (x given as FP32 bits) when bit b of mask is set: a bit test and a
+// predicated add, no select.  b is a compile-time constant at every call.
+__device__ __forceinline__ void add_if_bit(float& acc, uint32_t x, uint32_t mask, int b) {
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.b32 p, t, 0;\n\t"
+        "@p add.f32 %0, %0, %1;\n\t}"
+        : "+f"(acc)
+        : "f"(__uint_as_float(x)), "r"(mask), "r"(1u << b));
+}
+
+// Reduce-scatter over the 8 lanes that share lane % 4 (exchanges across lane
+// bits 4, 3, 2): lane l returns the sum of v[(l >> 2) & 7] over those lanes,
+// in a fixed summation tree.
+__device__ __forceinline__ float reduce_scatter8(float (&v)[8], uint32_t lane) {
 #pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
-        const bool upper = (lane & (uint32_t)half) != 0;
+    for (int half = 4, sh = 16; half >= 1; half >>= 1, sh >>= 1) {
+        const bool upper = (lane & (uint32_t)sh) != 0;
 #pragma unroll
         for (int k = 0; k < half; ++k) {
             const float send = upper ? v[k] : v[k + half];
             const float keep = upper ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
         }
     }
     return v[0];
@@ -487,7 +511,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_test(bar, parity)) return true;
+        if (mbar_sleep(bar, parity)) return true;
         if (obey_abort && *abort_flag) return false;
         if (clock64() - t0 > limit) {
             *abort_flag = 1;
@@ -702,11 +726,13 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         }
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------ epilogue
-        // Lane l of warp q4 owns accumulator columns c = 32 grp + l (grp = 0..7)
-        // for rows 32 q4 .. 32 q4 + 31: per drained chunk it sums its rows'
-        // selected values over the warp (FP32 butterfly), weights the column sum
-        // and accumulates it in FP64.  The four warps' FP64 column sums are
-        // added in a fixed order once per unit.
+        // Warp q4 drains TMEM lanes 32 q4 .. 32 q4 + 31.  Per drained chunk a
+        // thread loads four rows of 8 columns per 32-column group, keeps the
+        // selected entries and adds its rows; an exchange across the 8 lanes
+        // holding a column (FP32, fixed tree) leaves lane l with column
+        // 32 grp + l summed over the warp's 32 rows.  Column sums gather in
+        // FP32 over up to 4 chunks, then in FP64; each column is weighted once
+        // per unit, and the four warps' sums are added in a fixed order.
         const uint32_t et = threadIdx.x - 128;     // 0..127
         const uint32_t q4 = warp - 4;              // TMEM lane quarter
         const uint32_t row = q4 * 32 + lane;       // row within the band
@@ -741,26 +767,30 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 10, false)) { ok = false; break; }
                 ++epi_phase;
             }
-            // this row's selection masks for the unit: bit k of msk[grp] is set when
-            // accumulator column c = 32 grp + k is (p, g_p(row)) of a label row p
+            // selection masks for the unit.  Per 32-column group grp the lane holds
+            // column c = 32 grp + 4 m + (lane & 3) (m = 0..7) of the rows
+            // 32 q4 + lane / 4 + 8 a (a = 0..3); bit 4 m + a of msk[grp] is set when
+            // c is (p, g_p(row)) of a label row p: c < used and c % K == g_p(row).
             uint32_t msk[g::NMAX / 32];
             {
-                uint32_t p = 0, gcol = 0, lab = lab_rows[row];
+                const uint32_t rb = q4 * 32 + (lane >> 2);
+                uint32_t c = lane & 3u;
+                uint32_t p = c / K, gcol = c - p * K;
 #pragma unroll
                 for (int grp = 0; grp < g::NMAX / 32; ++grp) {
-                    uint32_t m = 0;
+                    uint32_t m32 = 0;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        if (32u * grp + k < used) {
-                            m |= (gcol == lab ? 1u : 0u) << k;
-                            if (++gcol == K) {
-                                gcol = 0;
-                                ++p;
-                                lab = p < a.ppt ? lab_rows[p * g::BM + row] : 0u;
-                            }
+                    for (int m = 0; m < 8; ++m) {
+                        if (c < used) {
+#pragma unroll
+                            for (int r4 = 0; r4 < 4; ++r4)
+                                m32 |= (lab_rows[p * g::BM + rb + 8 * r4] == gcol ? 1u : 0u) << (4 * m + r4);
                         }
+                        c += 4;
+                        gcol += 4;
+                        while (gcol >= K) { gcol -= K; ++p; }
                     }
-                    msk[grp] = m;
+                    msk[grp] = m32;
                 }
             }
             // every thread has its masks before overlapping column sums are written
@@ -769,18 +799,16 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 18, false)) { ok = false; break; }
                 ++epi_phase;
             }
-            // the group weights of this lane's columns (label row p0 + c/K, group c%K),
-            // divided by the band's scale S_I (a power of two: exact)
-            const double inv_s = __longlong_as_double((long long)(1023 - band_scale_exp(a.bmax[I])) << 52);
-            double wc[g::NMAX / 32], acc[g::NMAX / 32];
+            // column 32 grp + lane: FP32 sums of up to 4 drained chunks, then FP64
+            float colf[g::NMAX / 32];
+            double acc[g::NMAX / 32];
 #pragma unroll
             for (int grp = 0; grp < g::NMAX / 32; ++grp) {
-                const uint32_t c = 32u * grp + lane;
-                wc[grp] = (c < used && c / K < nlab)
-                              ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) * inv_s : 0.0;
+                colf[grp] = 0.f;
                 acc[grp] = 0.0;
             }
             const uint32_t nkb = NB - 2 * I;
+            uint32_t pending = 0;
             for (uint32_t c0 = 0; c0 < nkb; c0 += a.drain_kb, ++cc) {
                 const uint32_t b = (uint32_t)(cc & 1);
                 if (!lanes_wait(&acc_full[b], (uint32_t)(cc >> 1) & 1, abort_flag, st, 5)) { ok = false; break; }
@@ -789,24 +817,48 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 #pragma unroll
                 for (int grp = 0; grp < g::NMAX / 32; ++grp) {
                     if (32u * grp < a.N) {
-                        uint32_t r[32];
+                        uint32_t r0[16], r1[16];
                         __syncwarp();
-                        tmem_ld32(taddr + grp * 32, r);
+                        tmem_ld16x128_x8(taddr + grp * 32, r0);               // rows lane/4, +8
+                        tmem_ld16x128_x8(taddr + (16u << 16) + grp * 32, r1); // rows 16 + lane/4, +8
                         tmem_ld_wait();
-                        float v[32];
+                        const uint32_t mk = msk[grp];
+                        float v[8];
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) v[k] = (msk[grp] >> k) & 1u ? __uint_as_float(r[k]) : 0.f;
-                        // column 32 grp + lane summed over the warp's 32 rows
-                        acc[grp] = fma((double)reduce_scatter32(v, lane), wc[grp], acc[grp]);
+                        for (int m = 0; m < 8; ++m) {
+                            // rows in order lane/4, +8, +16, +24: add the selected ones
+                            v[m] = 0.f;
+                            add_if_bit(v[m], r0[2 * m], mk, 4 * m);
+                            add_if_bit(v[m], r0[2 * m + 1], mk, 4 * m + 1);
+                            add_if_bit(v[m], r1[2 * m], mk, 4 * m + 2);
+                            add_if_bit(v[m], r1[2 * m + 1], mk, 4 * m + 3);
+                        }
+                        // the 8 lanes holding a column add their rows: column 32 grp + lane
+                        colf[grp] += reduce_scatter8(v, lane);
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[b]);
+                if (++pending == 4) {
+                    pending = 0;
+#pragma unroll
+                    for (int grp = 0; grp < g::NMAX / 32; ++grp) {
+                        acc[grp] += (double)colf[grp];
+                        colf[grp] = 0.f;
+                    }
+                }
             }
             if (!ok) break;
-            // per label row: the four warps' column sums, then its K columns in group order
+            // each column weighted once: w_g / S_I for label row p0 + c / K, group c % K
+            // (S_I a power of two, so the division is exact)
+            const double inv_s = __longlong_as_double((long long)(1023 - band_scale_exp(a.bmax[I])) << 52);
 #pragma unroll
-            for (int grp = 0; grp < g::NMAX / 32; ++grp) acc64[q4 * g::NMAX + 32 * grp + lane] = acc[grp];
+            for (int grp = 0; grp < g::NMAX / 32; ++grp) {
+                const uint32_t c = 32u * grp + lane;
+                const double wc = (c < used && c / K < nlab)
+                                      ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) * inv_s : 0.0;
+                acc64[q4 * g::NMAX + c] = (acc[grp] + (double)colf[grp]) * wc;
+            }
             mbar_arrive(epi_bar);
             if (!lanes_wait(epi_bar, epi_phase & 1, abort_flag, st, 11, false)) { ok = false; break; }
             ++epi_phase;
@@ -832,6 +884,17 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         const uint32_t rows_used = a.ppt * K;
         const uint32_t pl = c / K, gg = c - pl * K;
         const uint32_t key = (0x4300u | gg) * 0x00010001u;   // (0x43gg, 0x43gg)
+        // the row's label chunk offsets in a label slice and its B-row store
+        // offsets in a B tile, the same for every k-block: chunk (q + pl/2) % 4
+        // at step q puts the up to 8 label rows a warp reads on distinct banks
+        uint32_t loff[4], soff[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
+            loff[q] = pl * g::BK + ch * 16;
+            soff[2 * q] = sw128_offset(c, 2 * ch);
+            soff[2 * q + 1] = sw128_offset(c, 2 * ch + 1);
+        }
         Ring rb, rl;
         bool ok = true;
         for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -848,12 +911,10 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 const uint8_t* L = lring + rl.idx * lab_bytes;
                 if (c < rows_used) {
                     // the label row's 64 bytes in four 16-byte chunks, each giving two 16-byte
-                    // chunks of the B row; chunk (q + pl/2) % 4 at step q puts the up to 8
-                    // label rows a warp reads on distinct banks
+                    // chunks of the B row
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
-                        const uint4 v = *reinterpret_cast<const uint4*>(L + pl * g::BK + ch * 16);
+                        const uint4 v = *reinterpret_cast<const uint4*>(L + loff[q]);
                         const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
@@ -867,8 +928,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                                 o[2 * hw] = f16x2_eq(lo, key);
                                 o[2 * hw + 1] = f16x2_eq(hi, key);
                             }
-                            *reinterpret_cast<uint4*>(B + sw128_offset(c, 2 * ch + h)) =
-                                make_uint4(o[0], o[1], o[2], o[3]);
+                            *reinterpret_cast<uint4*>(B + soff[2 * q + h]) = make_uint4(o[0], o[1], o[2], o[3]);
                         }
                     }
                 }

@@ -13,12 +13,15 @@
 // pass over the band before the split), y = S_I d^2, then split into
 //     h = bf16(y),   hi plane = bf16(2^7 h)  (exact),   lo plane = fp16(y - h)
 // (y - h is exact in FP32 and |y - h| <= 2^-8 y fits FP16), so hi + lo
-// carries 19 significant bits: relative error <= 2^-20 per term, or an
-// absolute 2^-25 / S_I (about 2^-48 x_max) where y - h is an FP16 subnormal.
-// The one-hot operand holds 0x3C00 where a label matches: FP16 1.0, and as
-// BF16 exactly 2^-7, so one B tile serves both planes: the hi MMA (BF16 A and
-// B) adds 2^7 h * 2^-7 = h, the lo MMA (FP16 A and B) adds y - h, into one
-// FP32 accumulator in tensor memory.  The accumulator is drained every
+// carries 19 significant bits: relative error <= 2^-20 per term as long as
+// the band's smallest nonzero d^2 is at least 2^-28 x_max (below that, y - h
+// of the small terms would be an FP16 subnormal).  A band with a wider range
+// stores lo = bf16(2^7 (y - h)) instead (16 significant bits in all, relative
+// error <= 2^-17 per term at any magnitude).  The one-hot operand holds
+// 0x3C00 where a label matches: FP16 1.0, and as BF16 exactly 2^-7, so one B
+// tile serves both planes: the hi MMA (BF16 A and B) adds 2^7 h * 2^-7 = h,
+// the lo MMA (FP16, or BF16 for a wide band) adds y - h, into one FP32
+// accumulator in tensor memory.  The accumulator is drained every
 // drain_kb k-blocks; the drained row values are weighted by w_g / S_I in
 // FP64, reduced over the 128 rows in a fixed order and accumulated in FP64.
 //
@@ -27,7 +30,8 @@
 // BF16) then the lo plane (128 x 64 FP16), each already in the tensor core's
 // K-major 128-byte swizzled layout, so one bulk copy (TMA engine) moves both
 // planes.  Entries with j <= i, i >= n or j >= n are zero.  After the tiles,
-// one 32-bit word per band holds the bit pattern of the band's largest d^2.
+// one 32-bit word per band holds the bit pattern of the band's largest d^2,
+// then one per band that of its smallest nonzero d^2.
 //
 // Kernel.  Persistent, one CTA per SM, 16 warps:
 //   warp 0       bulk-copies the A tiles into a 4-stage ring and the 64-column
@@ -256,6 +260,14 @@ __host__ __device__ __forceinline__ int band_scale_exp(uint32_t max_bits) {
     return s > 100 ? 100 : (s < -100 ? -100 : s);
 }
 
+// A band whose smallest nonzero d^2 is below 2^-28 of its largest keeps its lo
+// plane in BF16 (FP16 would lose the small terms to subnormals).
+__device__ __forceinline__ bool band_is_wide(uint32_t max_bits, uint32_t min_bits) {
+    if (min_bits == 0xFFFFFFFFu) return false;   // no nonzero entry
+    const float mx = __uint_as_float(max_bits), mn = __uint_as_float(min_bits);
+    return mn < mx * 3.7252902984619140625e-09f;   // 2^-28
+}
+
 // Byte offset of 16-byte chunk c (0..7) of row r inside a K-major 128-byte
 // swizzled tile (rows of 128 bytes, 8-row atoms of 1024 bytes).
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t c) {
@@ -291,7 +303,7 @@ static size_t tile_bytes_total(const GemmPlan& gp) {
 }
 
 size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
-    return tile_bytes_total(gp) + (size_t)gp.n_bands * sizeof(uint32_t);
+    return tile_bytes_total(gp) + 2 * (size_t)gp.n_bands * sizeof(uint32_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,31 +347,44 @@ __device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t
     }
 }
 
-// Largest d^2 of each band, as the bit pattern of a non-negative float
-// (bit order = value order), into bmax[I] (zeroed beforehand).
+// Largest and smallest nonzero d^2 of each band, as bit patterns of
+// non-negative floats (bit order = value order), into bmax[I] (zeroed
+// beforehand) and bmin[I] (set to all ones beforehand).
 __global__ void __launch_bounds__(256)
 k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
-                uint64_t t0, uint64_t t1, uint32_t* __restrict__ bmax) {
-    __shared__ uint32_t wmax[8];
+                uint64_t t0, uint64_t t1, uint32_t* __restrict__ bmax, uint32_t* __restrict__ bmin) {
+    __shared__ uint32_t wmax[8], wmin[8];
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         uint32_t I, kb;
         tile_coords(t, n_bands, I, kb);
         const bool diag = kb < 2 * I + 2;
-        uint32_t m = 0;
+        uint32_t m = 0, mn = 0xFFFFFFFFu;
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             float x[8];
             squared8(mat, n, ld, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) m = max(m, __float_as_uint(x[e]));
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t b = __float_as_uint(x[e]);
+                m = max(m, b);
+                if (b) mn = min(mn, b);
+            }
         }
         m = __reduce_max_sync(0xffffffffu, m);
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        if ((threadIdx.x & 31) == 0) {
+            wmax[threadIdx.x >> 5] = m;
+            wmin[threadIdx.x >> 5] = mn;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t b = wmax[0];
+            uint32_t b = wmax[0], c = wmin[0];
 #pragma unroll
-            for (int w = 1; w < 8; ++w) b = max(b, wmax[w]);
+            for (int w = 1; w < 8; ++w) {
+                b = max(b, wmax[w]);
+                c = min(c, wmin[w]);
+            }
             if (b) atomicMax(bmax + I, b);
+            if (c != 0xFFFFFFFFu) atomicMin(bmin + I, c);
         }
         __syncthreads();
     }
@@ -367,11 +392,13 @@ k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t
 
 __global__ void __launch_bounds__(256)
 k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
-            uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles, const uint32_t* __restrict__ bmax) {
+            uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles, const uint32_t* __restrict__ bmax,
+            const uint32_t* __restrict__ bmin) {
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         uint32_t I, kb;
         tile_coords(t, n_bands, I, kb);
         const float S = __uint_as_float((uint32_t)(127 + band_scale_exp(bmax[I])) << 23);
+        const bool wide = band_is_wide(bmax[I], bmin[I]);
         uint8_t* tile = tiles + t * g::TILE_BYTES;
         const bool diag = kb < 2 * I + 2;
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
@@ -387,7 +414,8 @@ k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_b
                     const float y = S * x[e + q];                    // exact: a power of two
                     const float h = __bfloat162float(__float2bfloat16_rn(y));
                     hb[q] = __bfloat16_as_ushort(__float2bfloat16_rn(h * 128.f));   // exact
-                    lb[q] = __half_as_ushort(__float2half_rn(y - h));             // y - h exact
+                    lb[q] = wide ? __bfloat16_as_ushort(__float2bfloat16_rn((y - h) * 128.f))
+                                 : __half_as_ushort(__float2half_rn(y - h));      // y - h exact
                 }
                 hw[e / 2] = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16);
                 lw[e / 2] = (uint32_t)lb[0] | ((uint32_t)lb[1] << 16);
@@ -410,10 +438,12 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
     const unsigned blocks = (unsigned)(n_tiles < 152ull * 16 ? n_tiles : 152ull * 16);
     uint8_t* tiles = (uint8_t*)scratch;
     uint32_t* bmax = reinterpret_cast<uint32_t*>(tiles + tile_bytes_total(gp));
+    uint32_t* bmin = bmax + gp.n_bands;
     cudaError_t e = cudaMemsetAsync(bmax + I0, 0, (size_t)(I1 - I0) * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bmin + I0, 0xFF, (size_t)(I1 - I0) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, bmax);
-    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, tiles, bmax);
+    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, bmax, bmin);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, tiles, bmax, bmin);
     return launched(2);
 }
 
@@ -486,7 +516,8 @@ struct Ring {
 
 struct GemmArgs {
     const uint8_t* tiles;      // prepared A tiles
-    const uint32_t* bmax;      // per band: bit pattern of the largest d^2 (sets S_I)
+    const uint32_t* bmax;      // per band: bit pattern of the largest d^2 (sets S_I),
+                               // then per band that of the smallest nonzero d^2
     const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
     const double* w;
     uint64_t w_set_rows;       // label rows per weight set (0: one set)
@@ -681,13 +712,16 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc_hi = idesc_bf16(g::BM, a.N), idesc_lo = idesc_f16(g::BM, a.N);
+            const uint32_t idesc_hi = idesc_bf16(g::BM, a.N);
             uint64_t cc = 0;
             Ring ra, rb;
             bool ok = true;
             for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint32_t nkb = NB - 2 * I;
+                // the band's lo plane is FP16, or BF16 where its range is too wide
+                const uint32_t idesc_lo = band_is_wide(a.bmax[I], a.bmax[a.n_bands + I])
+                                              ? idesc_bf16(g::BM, a.N) : idesc_f16(g::BM, a.N);
                 for (uint32_t c0 = 0; c0 < nkb && ok; c0 += a.drain_kb, ++cc) {
                     const uint32_t b = (uint32_t)(cc & 1);
                     if (!wait_bar(&acc_empty[b], ((uint32_t)(cc >> 1) & 1) ^ 1, abort_flag, st, 2)) {

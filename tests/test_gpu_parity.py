@@ -191,6 +191,35 @@ def test_constant_matrix_closed_form(ctx, form, n, K, c):
     np.testing.assert_allclose(got, np.full(rows.shape[0], want), rtol=RTOL)
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_tight_clusters_far_apart(ctx, form):
+    """Three clusters whose within-cluster distances are ~1e-5 of the distances
+    between them: each band's d^2 spans ~2^33, and s_W of the observed labels
+    (row 0) is made only of the tiny within-cluster terms."""
+    rng = np.random.default_rng(31)
+    n, K = 1500, 3
+    lab = np.arange(n) % K
+    centers = rng.standard_normal((K, 6)) * 10.0
+    X = centers[lab] + 1e-5 * rng.standard_normal((n, 6))
+    D = synth.euclidean_matrix(X)
+    rows = np.stack([lab] + [rng.permutation(lab) for _ in range(39)]).astype(np.int32)
+    w = synth.inv_sizes(lab, K)
+    ref = oracle.sW_alg1(D, rows, K, np.asarray(w, dtype=np.float64))
+    got = _run_sW(ctx, D, rows, K, w, form)
+    np.testing.assert_allclose(got, ref, rtol=RTOL)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("scale", [1e-15, 1e15])
+def test_extreme_scales(ctx, form, scale):
+    """D scaled by 1e-15 or 1e15 (d^2 from 1e-30 to 1e30, normal FP32): s_W
+    scales by scale^2 exactly (Sec. 1's definition is homogeneous of degree 2)."""
+    D, rows, w = _case(900, 4, 40, seed=41)
+    ref = oracle.sW_alg1(D, rows, 4, np.asarray(w, dtype=np.float64))
+    got = _run_sW(ctx, (D.astype(np.float64) * scale).astype(np.float32), rows, 4, w, form)
+    np.testing.assert_allclose(got / scale ** 2, ref, rtol=RTOL)
+
+
 def test_permutations_bit_exact_with_oracle(ctx):
     obs = synth.observed_labels([37, 20, 13, 3], 12)
     n = obs.size

@@ -501,6 +501,21 @@ def main():
 
         e2e_step()
         barrier()
+        # this machine's host->device copy rate from the same pinned buffer (2 GiB, 3 copies):
+        # the end-to-end step cannot beat max(kernel time, copy time of the step's bytes)
+        probe_n = min(Dh.numel(), (2 << 30) // 4)
+        probe_src = Dh.view(-1)[:probe_n]
+        probe_dst = torch.empty(probe_n, dtype=torch.float32, device=f"cuda:{dev}")
+        probe_dst.copy_(probe_src, non_blocking=True)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        for _ in range(3):
+            probe_dst.copy_(probe_src, non_blocking=True)
+        eb.record()
+        eb.synchronize()
+        h2d_gbs = 3 * probe_n * 4 / (ea.elapsed_time(eb) / 1e3) / 1e9
+        del probe_dst
+        torch.cuda.empty_cache()
         e2e_sampler = ClockSampler(gpu_query_id(torch, dev))
         e2e_sampler.start()
         t0 = time.perf_counter()
@@ -515,7 +530,7 @@ def main():
         e2e = {"value": pairs * rows_e2e / te, "unit": UNIT,
                "h2d_bytes_per_step": int(host_matrix_bytes(n) + B * n + K * 4),
                "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps, "step_ms": step_ms,
-               "clocks": e2e_clocks,
+               "clocks": e2e_clocks, "h2d_gbs": round(h2d_gbs, 1),
                "api": "permanova_sW_host (pinned host D, labels, weights, results; "
                       "copies D's band trapezoids in segments overlapped with the kernels)"}
 

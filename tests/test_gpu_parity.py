@@ -193,20 +193,29 @@ def test_constant_matrix_closed_form(ctx, form, n, K, c):
 
 @pytest.mark.parametrize("form", FORMS)
 def test_tight_clusters_far_apart(ctx, form):
-    """Three clusters whose within-cluster distances are ~1e-5 of the distances
-    between them: each band's d^2 spans ~2^33, and s_W of the observed labels
-    (row 0) is made only of the tiny within-cluster terms."""
+    """Three clusters: every within-cluster distance is eps = 3.1e-5, the
+    distances between clusters lie in [5, 12].  Each band's d^2 then spans
+    ~2^37, and s_W of the observed labels (row 0) consists only of the equal
+    tiny terms, so any rounding of them errs the same way for every pair:
+    s_W = eps^2 sum_g w_g n_g (n_g - 1) / 2 exactly (Sec. 1's definition).
+    The permuted rows are checked against the oracle."""
     rng = np.random.default_rng(31)
     n, K = 1500, 3
     lab = np.arange(n) % K
-    centers = rng.standard_normal((K, 6)) * 10.0
-    X = centers[lab] + 1e-5 * rng.standard_normal((n, 6))
-    D = synth.euclidean_matrix(X)
+    eps = np.float32(3.1e-5)
+    B = rng.uniform(5.0, 12.0, (n, n))
+    D = np.triu(B, 1)
+    D = (D + D.T).astype(np.float32)
+    D[lab[:, None] == lab[None, :]] = eps
+    np.fill_diagonal(D, 0.0)
     rows = np.stack([lab] + [rng.permutation(lab) for _ in range(39)]).astype(np.int32)
     w = synth.inv_sizes(lab, K)
-    ref = oracle.sW_alg1(D, rows, K, np.asarray(w, dtype=np.float64))
+    sizes = np.bincount(lab, minlength=K)
+    want0 = float(eps) ** 2 * sum(float(np.float32(w[g])) * sizes[g] * (sizes[g] - 1) / 2 for g in range(K))
+    ref = oracle.sW_alg1(D, rows[1:], K, np.asarray(w, dtype=np.float64))
     got = _run_sW(ctx, D, rows, K, w, form)
-    np.testing.assert_allclose(got, ref, rtol=RTOL)
+    np.testing.assert_allclose(got[0], want0, rtol=RTOL)
+    np.testing.assert_allclose(got[1:], ref, rtol=RTOL)
 
 
 @pytest.mark.parametrize("form", FORMS)

@@ -20,8 +20,9 @@
 //     pipe sees two operations per 512 evaluations.  Worst-case relative
 //     error of a group: about 28 unit roundoffs (16-term chains, the partial
 //     reduction, the weight's rounding and product, the 8-row chain), 1.7e-6;
-//     the next row's label is fetched one row ahead; the CTA writes one FP64
-//     partial per (band, label row).
+//     each thread's 64 row labels are staged in shared memory once per CTA
+//     (not re-read from global memory for every column tile); the CTA writes
+//     one FP64 partial per (band, label row).
 // Labels arrive as uint8 (K <= 256) or uint16 codes whose row stride is a
 // multiple of 16 bytes, so each thread loads its 64 column labels of a full
 // tile with 16-byte loads (the ragged last tile uses guarded scalar loads).
@@ -32,6 +33,10 @@ namespace pmn {
 constexpr int PB_P = 128;  // label rows per CTA (one per thread)
 constexpr int PB_T = 64;   // band height and column-tile width
 constexpr int PB_G = 8;    // rows per FP32 group sum
+constexpr uint32_t PB_D2_BYTES = PB_T * PB_T * 4;   // 16 KB
+constexpr uint32_t PB_W_BYTES = PB_T * PB_P * 4;    // 32 KB
+template <typename L>
+constexpr uint32_t pb_smem_bytes() { return PB_D2_BYTES + PB_W_BYTES + PB_T * PB_P * sizeof(L); }
 
 __device__ __forceinline__ float code_u8(uint32_t word, int k) {
     // bytes: [label byte k, 0, 0, 0x4B] -> float 2^23 + label
@@ -88,8 +93,12 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
                uint64_t lstride, uint64_t P, const double* __restrict__ w_all, uint64_t w_set_rows,
                uint32_t K,
                uint32_t n_pblocks, double* __restrict__ partials, const DevStatus* __restrict__ st) {
-    __shared__ __align__(16) float d2[PB_T][PB_T];
-    __shared__ float wrow[PB_T][PB_P];  // this thread's row weights, FP32
+    // dynamic shared memory: the D^2 tile, then per (row, thread) the row's
+    // FP32 weight and its label (clamped to K - 1)
+    extern __shared__ __align__(16) uint8_t pb_smem[];
+    float (*d2)[PB_T] = reinterpret_cast<float (*)[PB_T]>(pb_smem);
+    float (*wrow)[PB_P] = reinterpret_cast<float (*)[PB_P]>(pb_smem + PB_D2_BYTES);
+    L (*lrow)[PB_P] = reinterpret_cast<L (*)[PB_P]>(pb_smem + PB_D2_BYTES + PB_W_BYTES);
     const uint32_t band = blockIdx.x / n_pblocks;
     const uint32_t q = blockIdx.x % n_pblocks;
     const uint64_t p = (uint64_t)q * PB_P + threadIdx.x;
@@ -104,8 +113,11 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     const uint32_t r0 = band * PB_T;
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     double total = 0.0;
-    for (uint32_t r = 0; r < rows; ++r)
-        wrow[r][threadIdx.x] = (float)__ldg(w + min((uint32_t)g[r0 + r], K - 1));
+    for (uint32_t r = 0; r < rows; ++r) {
+        const uint32_t gr = min((uint32_t)g[r0 + r], K - 1);
+        lrow[r][threadIdx.x] = (L)gr;
+        wrow[r][threadIdx.x] = (float)__ldg(w + gr);
+    }
 
     for (uint32_t j0 = r0; j0 < n; j0 += PB_T) {
         __syncthreads();  // the previous tile has been consumed
@@ -142,14 +154,11 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
         }
         __syncthreads();
 
-        uint32_t gnext = min((uint32_t)g[r0], K - 1);
         for (uint32_t rg = 0; rg < rows; rg += PB_G) {
             const uint32_t rend = min(rg + PB_G, rows);
             float group = 0.f;
             for (uint32_t r = rg; r < rend; ++r) {
-                const uint32_t gi = gnext;
-                if (r + 1 < rows) gnext = min((uint32_t)g[r0 + r + 1], K - 1);   // prefetch
-                const float fgi = code_of(gi);
+                const float fgi = code_of(lrow[r][threadIdx.x]);
                 const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
                 float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -181,12 +190,18 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
     const uint64_t n_pblocks = (pr.P + PB_P - 1) / PB_P;
     const uint64_t blocks = (uint64_t)n_bands * n_pblocks;
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    const uint32_t smem = pb_smem_bytes<L>();
+    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sw_permblock<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     if (vec)
-        k_sw_permblock<L, true><<<(unsigned)blocks, PB_P, 0, s>>>(
+        k_sw_permblock<L, true><<<(unsigned)blocks, PB_P, smem, s>>>(
             pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
             (uint32_t)n_pblocks, partials, st);
     else
-        k_sw_permblock<L, false><<<(unsigned)blocks, PB_P, 0, s>>>(
+        k_sw_permblock<L, false><<<(unsigned)blocks, PB_P, smem, s>>>(
             pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
             (uint32_t)n_pblocks, partials, st);
     return launched(1);

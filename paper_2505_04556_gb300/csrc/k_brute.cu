@@ -37,7 +37,9 @@ k_sw_brute(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __re
     const uint64_t p = unit / n_chunks;
     const uint32_t c = (uint32_t)(unit % n_chunks);
     if (p >= P) return;
-    if (st->code != DEV_OK) {  // labels failed validation: skip the work
+    // labels failed validation: skip the work (a block-uniform vote, so the
+    // barrier in the block sum is never left by only some threads)
+    if (__syncthreads_or(st->code != DEV_OK)) {
         if (threadIdx.x == 0) partials[(uint64_t)c * P + p] = 0.0;
         return;
     }

@@ -103,7 +103,9 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     const uint32_t q = blockIdx.x % n_pblocks;
     const uint64_t p = (uint64_t)q * PB_P + threadIdx.x;
     const bool active = p < P;
-    if (st->code != DEV_OK) {
+    // a recorded device error skips the work; the vote keeps the exit uniform
+    // across the block even if the status word changes while threads read it
+    if (__syncthreads_or(st->code != DEV_OK)) {
         if (active) partials[(uint64_t)band * P + p] = 0.0;
         return;
     }

@@ -169,8 +169,11 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
  * copies run on a stream of the context, ordered after the work already queued
  * on `stream`; with the tensor-core form the bands are copied in up to 16
  * segments and each segment's kernels start as soon as it has landed, so the
- * copies overlap the computation.  Errors as permanova_sW, plus any error the
- * device reported (the call synchronises). */
+ * copies overlap the computation.  Segments alternate between `stream` and a
+ * second stream of the context (joined back into `stream` before the final
+ * reduction), so one segment's last wave of blocks overlaps the next
+ * segment's first.  Errors as permanova_sW, plus any error the device
+ * reported (the call synchronises). */
 int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
                       const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
                       const float *inv_group_sizes, double *out_sW, void *stream);

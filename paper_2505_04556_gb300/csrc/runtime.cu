@@ -51,9 +51,13 @@ struct permanova_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     uint64_t launch_mark = 0;
     int last_form = 0;
-    // host entry point: copies run on their own stream, ordered by events
+    // host entry point: copies run on their own stream, ordered by events;
+    // matrix segments alternate between the caller's stream and seg_stream so
+    // that one segment's last wave overlaps the next segment's first
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> copy_events;
+    cudaStream_t seg_stream = nullptr;
+    cudaEvent_t seg_fork = nullptr, seg_join = nullptr;
 };
 
 namespace {
@@ -255,6 +259,8 @@ struct Arrival {
     cudaEvent_t lab_ready = nullptr;
     std::vector<uint32_t> band;
     std::vector<cudaEvent_t> seg_ready;
+    cudaStream_t s2 = nullptr;                 // second stream for odd segments
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // The s_W path on device buffers; the arena is already large enough.
@@ -326,14 +332,23 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                 rc = profile_end(ctx, s);
                 if (rc) return rc;
             } else {
+                // segments alternate between s and s2 (disjoint bands: disjoint tiles,
+                // band words and partial rows), so a segment's last wave overlaps the
+                // next segment's first; s2 starts after everything queued on s so far
+                // and s continues after all of s2's work
+                CK(cudaEventRecord(arr->fork, s), "fork segment streams");
+                CK(cudaStreamWaitEvent(arr->s2, arr->fork, 0), "fork segment streams");
                 for (size_t k = 0; k + 1 < arr->band.size(); ++k) {
-                    CK(cudaStreamWaitEvent(s, arr->seg_ready[k], 0), "wait for a matrix segment");
-                    CK(launch_gemm_prep(q, gp, gs, s, arr->band[k], arr->band[k + 1]),
+                    cudaStream_t sk = (k & 1) ? arr->s2 : s;
+                    CK(cudaStreamWaitEvent(sk, arr->seg_ready[k], 0), "wait for a matrix segment");
+                    CK(launch_gemm_prep(q, gp, gs, sk, arr->band[k], arr->band[k + 1]),
                        "GEMM operand preparation");
-                    CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s, arr->band[k],
+                    CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, sk, arr->band[k],
                                         arr->band[k + 1]),
                        "GEMM kernel");
                 }
+                CK(cudaEventRecord(arr->join, arr->s2), "join segment streams");
+                CK(cudaStreamWaitEvent(s, arr->join, 0), "join segment streams");
             }
         }
     }
@@ -402,6 +417,9 @@ void permanova_destroy(permanova_ctx* ctx) {
         if (ctx->arena) cudaFree(ctx->arena);
         for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
         if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        if (ctx->seg_fork) cudaEventDestroy(ctx->seg_fork);
+        if (ctx->seg_join) cudaEventDestroy(ctx->seg_join);
+        if (ctx->seg_stream) cudaStreamDestroy(ctx->seg_stream);
         if (ctx->status) cudaFree(ctx->status);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
     }
@@ -634,6 +652,10 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     const uint32_t n_seg = L.form == PERMANOVA_FORM_GEMM ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
     if (!ctx->copy_stream)
         CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "create copy stream");
+    if (!ctx->seg_stream)
+        CK(cudaStreamCreateWithFlags(&ctx->seg_stream, cudaStreamNonBlocking), "create segment stream");
+    if (!ctx->seg_fork) CK(cudaEventCreateWithFlags(&ctx->seg_fork, cudaEventDisableTiming), "create event");
+    if (!ctx->seg_join) CK(cudaEventCreateWithFlags(&ctx->seg_join, cudaEventDisableTiming), "create event");
     while (ctx->copy_events.size() < kHostSegments + 2) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create copy event");
@@ -642,6 +664,9 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     cudaStream_t cs = ctx->copy_stream;
     Arrival arr;
     arr.lab_ready = ctx->copy_events[0];
+    arr.s2 = ctx->seg_stream;
+    arr.fork = ctx->seg_fork;
+    arr.join = ctx->seg_join;
     cudaEvent_t start = ctx->copy_events[1];
     CK(cudaEventRecord(start, s), "record start");
     CK(cudaStreamWaitEvent(cs, start, 0), "order copies after earlier work");

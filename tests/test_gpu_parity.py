@@ -229,6 +229,31 @@ def test_extreme_scales(ctx, form, scale):
     np.testing.assert_allclose(got / scale ** 2, ref, rtol=RTOL)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("fill", [3e30, float("nan")])
+def test_lower_triangle_never_read(ctx, form, fill):
+    """Entries on and below the diagonal take no part (Algorithm 1 sums i < j
+    only): huge or NaN values there change nothing, not even the tensor-core
+    form's per-band scale, which comes from each band's largest d^2."""
+    D, rows, w = _case(700, 3, 40, seed=43)
+    Dg = D.copy()
+    Dg[np.tril_indices(D.shape[0])] = fill
+    ref = oracle.sW_alg1(D, rows, 3, np.asarray(w, dtype=np.float64))
+    got = _run_sW(ctx, Dg, rows, 3, w, form)
+    np.testing.assert_allclose(got, ref, rtol=RTOL)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_all_zero_matrix(ctx, form):
+    """d = 0 everywhere gives s_W = 0 exactly (every band's largest d^2 is 0:
+    the tensor-core form's scale falls back to 1)."""
+    n = 600
+    rows = np.stack([np.random.default_rng(9).permutation(np.arange(n) % 4) for _ in range(33)])
+    got = _run_sW(ctx, np.zeros((n, n), dtype=np.float32), rows.astype(np.int32), 4,
+                  [0.25, 0.25, 0.25, 0.25], form)
+    assert np.all(got == 0.0)
+
+
 def test_permutations_bit_exact_with_oracle(ctx):
     obs = synth.observed_labels([37, 20, 13, 3], 12)
     n = obs.size

@@ -43,7 +43,9 @@
 //                thread), keep column (p, g_p(i)) of each row, reduce over rows,
 //                weight each column once per unit;
 //   warps 8-15   build the one-hot B tile (2-stage ring) from the labels, one
-//                B row per thread.
+//                B row per thread; for even K, two B rows of a label row per
+//                thread (one label read and byte permute for both), warps 8-11
+//                building stage 0 and warps 12-15 stage 1.
 // Work unit = (band I, tile of up to 128 label rows), band-major so the CTAs
 // running together share a band and read its A tiles from L2.
 // Every wait is bounded; on timeout the kernel records DEV_TIMEOUT, lets the
@@ -619,12 +621,12 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             mbar_init(&aempty[s], 1);
         }
         for (int s = 0; s < g::NBS; ++s) {
-            mbar_init(&ready[s], g::BUILDERS);
+            mbar_init(&ready[s], (a.K & 1u) ? g::BUILDERS : g::BUILDERS / 2);
             mbar_init(&bempty[s], 1);
         }
         for (uint32_t l = 0; l < g::NL_MAX; ++l) {
             mbar_init(&lfull[l], 1);
-            mbar_init(&lempty[l], g::BUILDERS);
+            mbar_init(&lempty[l], (a.K & 1u) ? g::BUILDERS : g::BUILDERS / 2);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -916,6 +918,74 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         const uint32_t c = threadIdx.x - 256;      // 0..255
         const uint32_t K = a.K;
         const uint32_t rows_used = a.ppt * K;
+        if ((K & 1u) == 0) {
+            // Even K: the label rows' K B rows pair up as (g, g + 1), g even, and
+            // one thread builds both from one read and byte permute of the labels.
+            // Warps 8-11 build the tiles of B stage 0, warps 12-15 those of stage 1
+            // (every other k-block), 128 threads per tile.
+            const uint32_t grp = c >> 7, t = c & 127u;
+            const uint32_t halfk = K >> 1;
+            const uint32_t pl = t / halfk, g0 = 2 * (t - pl * halfk);
+            const bool busy = pl < a.ppt;
+            const uint32_t row0 = pl * K + g0;
+            const uint32_t key0 = (0x4300u | g0) * 0x00010001u, key1 = (0x4300u | (g0 + 1)) * 0x00010001u;
+            uint32_t loff[4], s0[8], s1[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
+                loff[q] = pl * g::BK + ch * 16;
+                s0[2 * q] = sw128_offset(row0, 2 * ch);
+                s0[2 * q + 1] = sw128_offset(row0, 2 * ch + 1);
+                s1[2 * q] = sw128_offset(row0 + 1, 2 * ch);
+                s1[2 * q + 1] = sw128_offset(row0 + 1, 2 * ch + 1);
+            }
+            Ring rb, rl;
+            bool ok = true;
+            uint32_t seq = 0;   // k-blocks of this CTA so far: stage seq % 2
+            for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+                const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
+                const uint32_t nkb = NB - 2 * I;
+                for (uint32_t k = 0; k < nkb; ++k, ++seq) {
+                    if ((seq & 1u) == grp) {
+                        if (!wait_bar(&lfull[rl.idx], rl.phase, abort_flag, st, 6) ||
+                            !wait_bar(&bempty[rb.idx], rb.phase ^ 1, abort_flag, st, 13)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* B = sm + g::OFF_B + rb.idx * g::B_BYTES;
+                        const uint8_t* L = lring + rl.idx * lab_bytes;
+                        if (busy) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const uint4 v = *reinterpret_cast<const uint4*>(L + loff[q]);
+                                const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    uint32_t o0[4], o1[4];
+#pragma unroll
+                                    for (int hw = 0; hw < 2; ++hw) {
+                                        const uint32_t x = xs[2 * h + hw];
+                                        const uint32_t lo = __byte_perm(x, 0x43u, 0x4140u);
+                                        const uint32_t hi = __byte_perm(x, 0x43u, 0x4342u);
+                                        o0[2 * hw] = f16x2_eq(lo, key0);
+                                        o0[2 * hw + 1] = f16x2_eq(hi, key0);
+                                        o1[2 * hw] = f16x2_eq(lo, key1);
+                                        o1[2 * hw + 1] = f16x2_eq(hi, key1);
+                                    }
+                                    *reinterpret_cast<uint4*>(B + s0[2 * q + h]) = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+                                    *reinterpret_cast<uint4*>(B + s1[2 * q + h]) = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+                                }
+                            }
+                        }
+                        fence_proxy_async();
+                        mbar_arrive(&ready[rb.idx]);
+                        mbar_arrive(&lempty[rl.idx]);
+                    }
+                    rb.next(g::NBS);
+                    rl.next(NL);
+                }
+            }
+        } else {
         const uint32_t pl = c / K, gg = c - pl * K;
         const uint32_t key = (0x4300u | gg) * 0x00010001u;   // (0x43gg, 0x43gg)
         // the row's label chunk offsets in a label slice and its B-row store
@@ -972,6 +1042,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 rb.next(g::NBS);
                 rl.next(NL);
             }
+        }
         }
     }
 

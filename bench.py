@@ -220,7 +220,7 @@ def roofline(form: str, K: int, evals_per_launch: float, kernel_ms: float, pk: d
              traffic: float | None) -> dict:
     s = kernel_ms / 1e3
     if form == "gemm":
-        flops = 4.0 * K * evals_per_launch          # two BF16 planes x 2K flops per pair-perm
+        flops = 4.0 * K * evals_per_launch          # two 16-bit planes (hi, lo) x 2K flops per pair-perm
         achieved = flops / s / 1e12
         peak = pk["bf16_tflops_sustained"]
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -540,7 +540,7 @@ def main():
         cpu = oracle_rate(cfg, X, rows_h, 15.0)
 
     if rank == 0:
-        dtype = "bf16 hi+lo, f32 accumulate" if form == "gemm" else "f32"
+        dtype = "bf16 hi + fp16 lo, f32 accumulate" if form == "gemm" else "f32"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

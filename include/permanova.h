@@ -72,8 +72,10 @@ typedef enum {
  *              a block of 128 label rows (CUDA-core, issue-bound); the row
  *              weight is applied once per row segment as in Algorithm 2.
  *   GEMM       the dense-contraction form Z_p = (D o D) X_p with one-hot
- *              indicator columns X_p, on the tcgen05 tensor cores: D^2 split
- *              into BF16 hi + lo, FP32 accumulation in tensor memory, FP64
+ *              indicator columns X_p, on the tcgen05 tensor cores: D^2, scaled
+ *              by a power of two per 128-row band, split into a BF16 hi and an
+ *              FP16 lo part (BF16 where a band spans more than 2^28), FP32
+ *              accumulation in tensor memory drained every 512 columns, FP64
  *              partial sums.  Needs n_groups <= 256.
  *   AUTO       the planner's choice for (n, K, P): a bucket timed by
  *              permanova_autotune if there is one, else GEMM for K <= 36,

@@ -126,8 +126,9 @@ size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t P);
 size_t gemm_label_bytes(const GemmPlan& gp);
 cudaError_t launch_repack_gemm(const void* in, int in_type, uint32_t n, uint64_t P, uint32_t K,
                                const GemmPlan& gp, void* out, DevStatus* st, cudaStream_t s);
-// D^2 -> BF16 hi/lo operand tiles in the scratch, for the 128-row bands [I0, I1)
-// (a band's tiles are made from the band's rows of D only)
+// D^2 -> per-band scale, then BF16 hi / FP16 (or BF16) lo operand tiles in the
+// scratch, for the 128-row bands [I0, I1) (a band's tiles and scale are made from
+// the band's rows of D only)
 cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scratch, cudaStream_t s,
                              uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu);
 // the tensor-core kernel over bands [I0, I1): partials is gp.n_bands x P, this

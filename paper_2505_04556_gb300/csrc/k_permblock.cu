@@ -159,6 +159,8 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
         for (uint32_t rg = 0; rg < rows; rg += PB_G) {
             const uint32_t rend = min(rg + PB_G, rows);
             float group = 0.f;
+            // two rows per iteration: their compare/FMA streams interleave
+#pragma unroll 2
             for (uint32_t r = rg; r < rend; ++r) {
                 const float fgi = code_of(lrow[r][threadIdx.x]);
                 const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);

@@ -169,7 +169,8 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
     Algorithm 1 on all host threads (the reported value, one label row per
     thread, the row count sized so the run takes about ``target_s`` seconds),
     Algorithm 1 on one thread, and Algorithm 2 (tiled, 64 x 64) on all
-    threads (with ``extras``), each a bounded sample of label rows."""
+    threads and, as the paper's CPU method, in FP32 (with ``extras``), each a
+    bounded sample of label rows."""
     import oracle
     T = oracle.max_threads()
     K = cfg["K"]
@@ -187,8 +188,10 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
         t0 = time.perf_counter()
         if alg == 1:
             oracle.sW_alg1(D, rows, K, w, threads=threads)
-        else:
+        elif alg == 2:
             oracle.sW_alg2(D, rows, K, w, 64, threads=threads)
+        else:
+            oracle.sW_alg2_f32(D, rows, K, w, 64, threads=threads)
         return time.perf_counter() - t0
 
     R = T
@@ -207,10 +210,14 @@ def oracle_rate(cfg: dict, X: np.ndarray, label_rows: np.ndarray, target_s: floa
         r1 = max(1, min(8, int(round(target_s / 3 * rate / T / pairs_s))))
         t1 = run(r1, 1)
         t2 = run(T, T, alg=2)
+        t3 = run(T, T, alg=3)
         res["single_thread"] = {"value": r1 * pairs_s / t1,
                                 "sample": f"Algorithm 1, {r1} label rows, 1 thread, {t1:.1f} s"}
         res["alg2_tiled"] = {"value": T * pairs_s / t2, "sample": f"Algorithm 2 (64 x 64 tiles), "
                              f"{T} label rows, {T} threads, {t2:.1f} s"}
+        res["alg2_tiled_fp32"] = {"value": T * pairs_s / t3,
+                                  "sample": f"the paper's CPU method: Algorithm 2 (64 x 64 tiles) "
+                                            f"with FP32 values, {T} label rows, {T} threads, {t3:.1f} s"}
         res["cpu_model"] = cpu_model()
     return res
 
@@ -396,6 +403,7 @@ def main():
                                  "kind": "oracle", "sample": first["sample"],
                                  "single_thread": first.get("single_thread"),
                                  "alg2_tiled": first.get("alg2_tiled"),
+                                 "alg2_tiled_fp32": first.get("alg2_tiled_fp32"),
                                  "cpu_model": first.get("cpu_model")},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}

@@ -61,6 +61,8 @@ def _load():
         lib.oracle_sW_alg1.argtypes = [vp, c_u64, c_u64, vp, c_u64, c_u32, vp, vp, c_i32]
         lib.oracle_sW_alg1.restype = c_i32
         lib.oracle_sW_alg2.argtypes = [vp, c_u64, c_u64, vp, c_u64, c_u32, vp, c_u64, vp, c_i32]
+        lib.oracle_sW_alg2_f32.argtypes = [vp, c_u64, c_u64, vp, c_u64, c_u32, vp, c_u64, vp, c_i32]
+        lib.oracle_sW_alg2_f32.restype = c_i32
         lib.oracle_sW_alg2.restype = c_i32
         lib.oracle_sT.argtypes = [vp, c_u64, c_u64]
         lib.oracle_sT.restype = ctypes.c_double
@@ -126,6 +128,21 @@ def sW_alg2(mat, groupings, n_groups: int, inv_group_sizes, tile: int,
                                 int(tile), _ptr(out), int(threads))
     if rc:
         raise ValueError("oracle_sW_alg2: invalid input")
+    return out
+
+
+def sW_alg2_f32(mat, groupings, n_groups: int, inv_group_sizes, tile: int,
+                threads: int = 0) -> np.ndarray:
+    """Algorithm 2 in the listing's FP32 value types: the paper's CPU method,
+    for timing context only (not a parity reference)."""
+    m, n, ld = _mat(mat)
+    g = np.ascontiguousarray(np.atleast_2d(groupings), dtype=np.int32)
+    w = np.ascontiguousarray(inv_group_sizes, dtype=np.float32)
+    out = np.zeros(g.shape[0], dtype=np.float32)
+    rc = _load().oracle_sW_alg2_f32(_ptr(m), n, ld, _ptr(g), g.shape[0], int(n_groups), _ptr(w),
+                                    int(tile), _ptr(out), int(threads))
+    if rc:
+        raise ValueError("oracle_sW_alg2_f32: invalid input")
     return out
 
 

@@ -16,6 +16,11 @@
  *                    into TILE x TILE blocks (column blocks start at trow+1),
  *                    the row segment summed unweighted and multiplied by
  *                    inv_group_sizes once.  FP64 throughout.
+ *   oracle_sW_alg2_f32
+ *                    Algorithm 2 with the listing's FP32 value types (float
+ *                    accumulators and weights): the paper's CPU method, timed
+ *                    by the benchmark for context only; never a parity
+ *                    reference.
  *   oracle_sT        total sum of squares s_T = (1/n) sum_{i<j} d_ij^2, the
  *                    textbook PERMANOVA quantity (Sec. 1 refers to the method
  *                    [1-2]; the pre/post steps are described in Sec. 2 as
@@ -135,6 +140,48 @@ int oracle_sW_alg2(const float *mat, uint64_t n, uint64_t ld, const int32_t *gro
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < np; ++p)
         group_sWs[p] = sW_one_alg2(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
+    return ORACLE_OK;
+}
+
+/* Algorithm 2, one permutation, in the listing's FP32 value types. */
+static float sW_one_alg2_f32(const float *mat, uint64_t n, uint64_t ld,
+                             const int32_t *grouping, const float *inv_group_sizes,
+                             uint64_t tile) {
+    float s_W = 0.0f;
+    for (uint64_t trow = 0; trow + 1 < n; trow += tile) {
+        for (uint64_t tcol = trow + 1; tcol < n; tcol += tile) {
+            uint64_t row_end = trow + tile < n - 1 ? trow + tile : n - 1;
+            for (uint64_t row = trow; row < row_end; ++row) {
+                uint64_t min_col = tcol > row + 1 ? tcol : row + 1;
+                uint64_t max_col = tcol + tile < n ? tcol + tile : n;
+                const float *mat_row = mat + row * ld;
+                int32_t group_idx = grouping[row];
+                float local_s_W = 0.0f;
+                for (uint64_t col = min_col; col < max_col; ++col) {
+                    if (grouping[col] == group_idx) {
+                        float val = mat_row[col];
+                        local_s_W += val * val;
+                    }
+                }
+                s_W += local_s_W * inv_group_sizes[group_idx];
+            }
+        }
+    }
+    return s_W;
+}
+
+/* Driver of Algorithm 2 in FP32 (timing context only). */
+int oracle_sW_alg2_f32(const float *mat, uint64_t n, uint64_t ld, const int32_t *groupings,
+                       uint64_t n_perms, uint32_t n_groups, const float *inv_group_sizes,
+                       uint64_t tile, float *group_sWs, int n_threads) {
+    if (!mat || !groupings || !inv_group_sizes || !group_sWs || ld < n || n_groups == 0 || tile == 0)
+        return ORACLE_EINVAL;
+    if (!labels_valid(groupings, n, n_perms, n_groups)) return ORACLE_EINVAL;
+    set_threads(n_threads);
+    int64_t np = (int64_t)n_perms;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < np; ++p)
+        group_sWs[p] = sW_one_alg2_f32(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
     return ORACLE_OK;
 }
 

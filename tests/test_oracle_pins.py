@@ -166,6 +166,18 @@ def test_alg1_exact_on_integer_matrix_power_of_two_groups():
     assert Fraction(got) == exact
 
 
+def test_alg2_f32_close_to_fp64():
+    """The FP32 Algorithm 2 (the paper's CPU method, timed for context only)
+    agrees with the FP64 oracle to FP32 summation accuracy."""
+    D, lab = _random_case(300, 4, 23)
+    rows = synth.shuffled_rows(lab, 8, 24)
+    w = synth.inv_sizes(lab, 4)
+    ref = oracle.sW_alg1(D, rows, 4, w)
+    got = oracle.sW_alg2_f32(D, rows, 4, w, 64)
+    np.testing.assert_allclose(got.astype(np.float64), ref, rtol=1e-4)
+    assert not np.array_equal(got.astype(np.float64), ref)   # it is FP32, not FP64
+
+
 @pytest.mark.parametrize("tile", [1, 3, 7, 16, 64, 97])
 def test_alg1_equals_alg2(tile):
     D, lab = _random_case(97, 5, 11)

@@ -78,7 +78,7 @@ typedef enum {
  *              accumulation in tensor memory drained every 512 columns, FP64
  *              partial sums.  Needs n_groups <= 256.
  *   AUTO       the planner's choice for (n, K, P): a bucket timed by
- *              permanova_autotune if there is one, else GEMM for K <= 36,
+ *              permanova_autotune if there is one, else GEMM for K <= 32,
  *              n >= 256 and P >= 32, else PERMBLOCK for P >= 16, else BRUTE. */
 typedef enum {
     PERMANOVA_FORM_AUTO = 0,

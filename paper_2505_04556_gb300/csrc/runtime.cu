@@ -125,7 +125,7 @@ int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
     // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
     // Measured on a GB300 at n = 20,000 with 4,000 label rows: the GEMM form is
     // 2.5x the perm-block form at K = 16, 1.27x at K = 32 and 0.96x at K = 40.
-    if (gemm_available() && K <= 36 && n >= 256 && P >= 32) return PERMANOVA_FORM_GEMM;
+    if (gemm_available() && K <= 32 && n >= 256 && P >= 32) return PERMANOVA_FORM_GEMM;
     if (P >= 16 && K <= 65536) return PERMANOVA_FORM_PERMBLOCK;
     return PERMANOVA_FORM_BRUTE;
 }

@@ -87,7 +87,7 @@ def _case(n, K, P, seed, kind="euclid"):
                                    # several accumulator chunks per band, ragged label-row
                                    # tiles of 128 (K = 2) and 85 (K = 3) rows, 36 rows (K = 7)
                                    (2500, 2, 300), (2500, 3, 200), (3000, 7, 150),
-                                   # the planner's largest GEMM group count (7 label rows x 36)
+                                   # a large group count (7 label rows x 36)
                                    (700, 36, 50)])
 def test_sW_matches_oracle(ctx, form, n, K, P):
     D, rows, w = _case(n, K, P, seed=n * 7 + K)

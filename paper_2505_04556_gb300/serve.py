@@ -54,6 +54,30 @@ class Request:
         return self.t_done - self.t_arrival
 
 
+def take_batch(pending: "collections.deque[Request]", in_use: int, budget: int,
+               max_batch: int) -> tuple[list[Request], int]:
+    """Admission: the oldest waiting request, if its scratch fits the budget
+    left, plus the waiting requests that can share its launch (same matrix,
+    number of groups and permutations) and still fit, in arrival order, up to
+    ``max_batch``.  Removes them from ``pending``; returns the batch (empty if
+    the oldest does not fit) and the budget in use afterwards.  Requests carry
+    their scratch estimate as ``_need``."""
+    if not pending or pending[0]._need + in_use > budget:
+        return [], in_use
+    head = pending.popleft()
+    in_use += head._need
+    batch = [head]
+    key = (head.matrix_id, head.n_groups, head.n_perms)
+    for r in list(pending):
+        if len(batch) >= max_batch:
+            break
+        if (r.matrix_id, r.n_groups, r.n_perms) == key and in_use + r._need <= budget:
+            pending.remove(r)
+            in_use += r._need
+            batch.append(r)
+    return batch, in_use
+
+
 class Server:
     """``matrices``: dict id -> square fp32 CUDA tensor (resident)."""
 
@@ -113,20 +137,9 @@ class Server:
                 if not self.running:
                     self.free_slots.put(slot)
                     return
-                head = self.pending.popleft()
-                self.in_use += head._need
-                batch = [head]
-                # requests already waiting that can share the launch: same matrix,
-                # same number of groups and permutations (one s_W pass for all)
-                key = (head.matrix_id, head.n_groups, head.n_perms)
-                for r in list(self.pending):
-                    if len(batch) >= self.max_batch:
-                        break
-                    if ((r.matrix_id, r.n_groups, r.n_perms) == key
-                            and self.in_use + r._need <= self.budget):
-                        self.pending.remove(r)
-                        self.in_use += r._need
-                        batch.append(r)
+                # the oldest request plus the waiting ones that can share its launch
+                batch, self.in_use = take_batch(self.pending, self.in_use, self.budget,
+                                                self.max_batch)
             threading.Thread(target=self._run, args=(slot, batch), daemon=True).start()
 
     def _run(self, slot: int, batch: list[Request]):

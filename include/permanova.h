@@ -215,8 +215,8 @@ int permanova_sW_noalloc(const float *mat, uint32_t n_dims, uint64_t ld, const v
  * label), ETIMEOUT or ECUDA. */
 int permanova_sync(permanova_ctx *ctx, void *stream);
 
-/* Permutation labels for the test of Sec. 1 ("assignment of objects to
- * groups randomly permuted"), generated on the device:
+/* Permutation labels for the permutation test of Sec. 1 (the objects' group
+ * labels reassigned at random), generated on the device:
  *   grouping   DEVICE, n_dims int32 observed labels in [0, n_groups).
  *   out        DEVICE, (n_perms + 1) rows of n_dims labels of label_type;
  *              row 0 = grouping, row p >= 1 = an independent Fisher-Yates

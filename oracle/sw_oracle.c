@@ -8,14 +8,16 @@
  * generator with the CUDA library; the two meet only through seeded inputs.
  *
  * What each function follows:
- *   oracle_sW_alg1   Algorithm 1 (Sec. 2): every upper-triangle pair (row<col)
- *                    whose labels agree adds val*val*inv_group_sizes[label];
- *                    the driver loops over permutations, labels of
- *                    permutation p at groupings + p*n.  FP64 throughout.
- *   oracle_sW_alg2   Algorithm 2 (Sec. 2): the same sum with the triangle cut
- *                    into TILE x TILE blocks (column blocks start at trow+1),
- *                    the row segment summed unweighted and multiplied by
- *                    inv_group_sizes once.  FP64 throughout.
+ *   oracle_sW_alg1   the statistic of Algorithm 1 (Sec. 2) from its
+ *                    definition: d_ij^2 * w_{g(i)} summed over the pairs
+ *                    i < j in one group, pairs taken in row-major order;
+ *                    one label row per permutation, the label of object i
+ *                    in row p at groupings[p*n + i].  FP64 throughout.
+ *   oracle_sW_alg2   the blocked evaluation of Algorithm 2 (Sec. 2): row
+ *                    blocks and column blocks of TILE, the column blocks of
+ *                    a row block starting one column right of its first
+ *                    row, each row segment summed without weights and then
+ *                    weighted once.  FP64 throughout.
  *   oracle_sW_alg2_f32
  *                    Algorithm 2 with the listing's FP32 value types (float
  *                    accumulators and weights): the paper's CPU method, timed
@@ -26,8 +28,8 @@
  *                    [1-2]; the pre/post steps are described in Sec. 2 as
  *                    happening before and after s_W).
  *   oracle_philox4x32_10, oracle_permutations
- *                    the permutation test of Sec. 1 ("assignment of objects to
- *                    groups randomly permuted"): permutation p >= 1 is an
+ *                    the permutation test of Sec. 1 (the objects' group
+ *                    labels reassigned at random): permutation p >= 1 is an
  *                    independent Fisher-Yates shuffle of the observed labels
  *                    driven by Philox4x32-10 (Salmon et al., SC'11) keyed by
  *                    the seed with counter (block, 0, p, 0), bounded draws by
@@ -63,48 +65,68 @@ static int set_threads(int n_threads) {
 
 int oracle_max_threads(void) { return set_threads(0); }
 
-/* Algorithm 1, one permutation: FP64 sum over row < col with equal labels. */
-static double sW_one_alg1(const float *mat, uint64_t n, uint64_t ld,
-                          const int32_t *grouping, const double *inv_group_sizes) {
-    double s_W = 0.0;
-    for (uint64_t row = 0; row + 1 < n; ++row) {          /* last row has no columns */
-        const float *mat_row = mat + row * ld;
-        for (uint64_t col = row + 1; col < n; ++col) {    /* diagonal never read */
-            int32_t group_idx = grouping[row];
-            if (grouping[col] == group_idx) {
-                double val = (double)mat_row[col];
-                s_W += val * val * inv_group_sizes[group_idx];
-            }
+/* s_W of one labelling, written as its definition (Sec. 2, Algorithm 1's
+ * statistic): the sum of d_ij^2 * w_{g(i)} over every pair i < j whose two
+ * objects share a group.  The strict upper triangle is walked as a single
+ * sequence of pairs, ordered by first index and then by second index, and
+ * each qualifying pair's term is added to one FP64 accumulator in that
+ * order (the accumulation order of Algorithm 1). */
+static double within_ss_pairwise(const float *D, uint64_t n, uint64_t ld,
+                                 const int32_t *lab, const double *w) {
+    double acc = 0.0;
+    if (n < 2) return acc;
+    const uint64_t n_pairs = n * (n - 1) / 2;
+    uint64_t i = 0, j = 1;                 /* current pair (i, j), i < j */
+    for (uint64_t k = 0; k < n_pairs; ++k) {
+        const int32_t gi = lab[i];
+        if (lab[j] == gi) {
+            const double d = (double)D[i * ld + j];
+            acc += d * d * w[gi];
+        }
+        if (++j == n) {                    /* next first index */
+            ++i;
+            j = i + 1;
         }
     }
-    return s_W;
+    return acc;
 }
 
-/* Algorithm 2, one permutation: tiled, weight applied once per row segment. */
-static double sW_one_alg2(const float *mat, uint64_t n, uint64_t ld,
-                          const int32_t *grouping, const double *inv_group_sizes,
-                          uint64_t tile) {
-    double s_W = 0.0;
-    for (uint64_t trow = 0; trow + 1 < n; trow += tile) {
-        for (uint64_t tcol = trow + 1; tcol < n; tcol += tile) {
-            uint64_t row_end = trow + tile < n - 1 ? trow + tile : n - 1;
-            for (uint64_t row = trow; row < row_end; ++row) {
-                uint64_t min_col = tcol > row + 1 ? tcol : row + 1;
-                uint64_t max_col = tcol + tile < n ? tcol + tile : n;
-                const float *mat_row = mat + row * ld;
-                int32_t group_idx = grouping[row];
-                double local_s_W = 0.0;
-                for (uint64_t col = min_col; col < max_col; ++col) {
-                    if (grouping[col] == group_idx) {
-                        double val = (double)mat_row[col];
-                        local_s_W += val * val;
-                    }
-                }
-                s_W += local_s_W * inv_group_sizes[group_idx];
+/* Sum of d_ij^2 over the columns j in [lo, hi) of row i whose label equals
+ * g (no weight): one row segment of the blocked evaluation below. */
+static double row_segment(const float *D, uint64_t ld, const int32_t *lab, uint64_t i,
+                          uint64_t lo, uint64_t hi, int32_t g) {
+    double part = 0.0;
+    const float *Di = D + i * ld;
+    for (uint64_t j = lo; j < hi; ++j)
+        if (lab[j] == g) part += (double)Di[j] * (double)Di[j];
+    return part;
+}
+
+/* s_W of one labelling evaluated in blocks, as Algorithm 2 (Sec. 2)
+ * describes it: the rows are cut into blocks of `tile` rows; the columns a
+ * row block meets are cut into blocks of `tile` columns, the first starting
+ * one column right of the block's first row; in each (row block, column
+ * block) every row contributes the part of its segment that lies right of
+ * the diagonal, summed without weights, and the segment's sum is then
+ * multiplied once by the weight of the row's group. */
+static double within_ss_blocked(const float *D, uint64_t n, uint64_t ld,
+                                const int32_t *lab, const double *w, uint64_t tile) {
+    double acc = 0.0;
+    if (n < 2) return acc;
+    const uint64_t last_row = n - 1;       /* rows 0 .. n-2 own pairs */
+    for (uint64_t rb = 0; rb < last_row; rb += tile) {
+        const uint64_t rb_end = rb + tile < last_row ? rb + tile : last_row;
+        for (uint64_t cb = rb + 1; cb < n; cb += tile) {
+            const uint64_t cb_end = cb + tile < n ? cb + tile : n;
+            for (uint64_t i = rb; i < rb_end; ++i) {
+                const uint64_t lo = cb > i + 1 ? cb : i + 1;
+                if (lo >= cb_end) continue;    /* segment empty: adds 0 */
+                const int32_t g = lab[i];
+                acc += row_segment(D, ld, lab, i, lo, cb_end, g) * w[g];
             }
         }
     }
-    return s_W;
+    return acc;
 }
 
 static int labels_valid(const int32_t *groupings, uint64_t n, uint64_t n_perms, uint32_t n_groups) {
@@ -124,7 +146,7 @@ int oracle_sW_alg1(const float *mat, uint64_t n, uint64_t ld, const int32_t *gro
     int64_t np = (int64_t)n_perms;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < np; ++p)
-        group_sWs[p] = sW_one_alg1(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes);
+        group_sWs[p] = within_ss_pairwise(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes);
     return ORACLE_OK;
 }
 
@@ -139,35 +161,35 @@ int oracle_sW_alg2(const float *mat, uint64_t n, uint64_t ld, const int32_t *gro
     int64_t np = (int64_t)n_perms;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < np; ++p)
-        group_sWs[p] = sW_one_alg2(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
+        group_sWs[p] = within_ss_blocked(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
     return ORACLE_OK;
 }
 
-/* Algorithm 2, one permutation, in the listing's FP32 value types. */
-static float sW_one_alg2_f32(const float *mat, uint64_t n, uint64_t ld,
-                             const int32_t *grouping, const float *inv_group_sizes,
-                             uint64_t tile) {
-    float s_W = 0.0f;
-    for (uint64_t trow = 0; trow + 1 < n; trow += tile) {
-        for (uint64_t tcol = trow + 1; tcol < n; tcol += tile) {
-            uint64_t row_end = trow + tile < n - 1 ? trow + tile : n - 1;
-            for (uint64_t row = trow; row < row_end; ++row) {
-                uint64_t min_col = tcol > row + 1 ? tcol : row + 1;
-                uint64_t max_col = tcol + tile < n ? tcol + tile : n;
-                const float *mat_row = mat + row * ld;
-                int32_t group_idx = grouping[row];
-                float local_s_W = 0.0f;
-                for (uint64_t col = min_col; col < max_col; ++col) {
-                    if (grouping[col] == group_idx) {
-                        float val = mat_row[col];
-                        local_s_W += val * val;
-                    }
-                }
-                s_W += local_s_W * inv_group_sizes[group_idx];
+/* The blocked evaluation above with FP32 value types throughout (float
+ * accumulators, float weights), the precision the paper's CPU code uses;
+ * timing context only. */
+static float within_ss_blocked_f32(const float *D, uint64_t n, uint64_t ld,
+                                   const int32_t *lab, const float *w, uint64_t tile) {
+    float acc = 0.0f;
+    if (n < 2) return acc;
+    const uint64_t last_row = n - 1;
+    for (uint64_t rb = 0; rb < last_row; rb += tile) {
+        const uint64_t rb_end = rb + tile < last_row ? rb + tile : last_row;
+        for (uint64_t cb = rb + 1; cb < n; cb += tile) {
+            const uint64_t cb_end = cb + tile < n ? cb + tile : n;
+            for (uint64_t i = rb; i < rb_end; ++i) {
+                const uint64_t lo = cb > i + 1 ? cb : i + 1;
+                if (lo >= cb_end) continue;
+                const int32_t g = lab[i];
+                const float *Di = D + i * ld;
+                float part = 0.0f;
+                for (uint64_t j = lo; j < cb_end; ++j)
+                    if (lab[j] == g) part += Di[j] * Di[j];
+                acc += part * w[g];
             }
         }
     }
-    return s_W;
+    return acc;
 }
 
 /* Driver of Algorithm 2 in FP32 (timing context only). */
@@ -181,7 +203,7 @@ int oracle_sW_alg2_f32(const float *mat, uint64_t n, uint64_t ld, const int32_t 
     int64_t np = (int64_t)n_perms;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < np; ++p)
-        group_sWs[p] = sW_one_alg2_f32(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
+        group_sWs[p] = within_ss_blocked_f32(mat, n, ld, groupings + (uint64_t)p * n, inv_group_sizes, tile);
     return ORACLE_OK;
 }
 

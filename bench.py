@@ -509,22 +509,28 @@ def main():
 
         e2e_step()
         barrier()
-        # this machine's host->device copy rate from the same pinned buffer (2 GiB, 3 copies):
-        # the end-to-end step cannot beat max(kernel time, copy time of the step's bytes)
-        probe_n = min(Dh.numel(), (2 << 30) // 4)
-        probe_src = Dh.view(-1)[:probe_n]
+        # this machine's host->device copy rate from the same pinned buffer: 1 GiB
+        # copies (2 each) at five offsets across the whole buffer; the
+        # end-to-end step cannot beat max(kernel time, copy time of its bytes)
+        probe_n = min(Dh.numel(), (1 << 30) // 4)
         probe_dst = torch.empty(probe_n, dtype=torch.float32, device=f"cuda:{dev}")
-        probe_dst.copy_(probe_src, non_blocking=True)
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record()
-        for _ in range(3):
+        h2d_at = []
+        for frac in (0.0, 0.25, 0.5, 0.75, 1.0):
+            o = int(frac * (Dh.numel() - probe_n))
+            probe_src = Dh.view(-1)[o:o + probe_n]
             probe_dst.copy_(probe_src, non_blocking=True)
-        eb.record()
-        eb.synchronize()
-        h2d_gbs = 3 * probe_n * 4 / (ea.elapsed_time(eb) / 1e3) / 1e9
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record()
+            for _ in range(2):
+                probe_dst.copy_(probe_src, non_blocking=True)
+            eb.record()
+            eb.synchronize()
+            h2d_at.append(round(2 * probe_n * 4 / (ea.elapsed_time(eb) / 1e3) / 1e9, 1))
+        h2d_gbs = min(h2d_at)
         del probe_dst
         torch.cuda.empty_cache()
         e2e_sampler = ClockSampler(gpu_query_id(torch, dev))
+        pm.permanova_profile_enable(ctx.handle, True)
         e2e_sampler.start()
         t0 = time.perf_counter()
         step_ms = []
@@ -535,10 +541,21 @@ def main():
         barrier()
         te, rows_e2e = combine_ranks(time.perf_counter() - t0, float(B * args.e2e_steps))
         e2e_clocks = e2e_sampler.stop()
+        hp = pm.permanova_profile_read(ctx.handle)
+        pm.permanova_profile_enable(ctx.handle, False)
+        calls = max(1, hp["host_calls"])
+        # device-side timeline of one step (CUDA events, averaged over the steps)
+        timeline = {"device_ms": round(hp["host_total_ms"] / calls, 2),
+                    "first_segment_landed_ms": round(hp["host_first_segment_ms"] / calls, 2),
+                    "last_segment_landed_ms": round(hp["host_copy_ms"] / calls, 2),
+                    "h2d_gbs_in_step": round(hp["host_h2d_bytes"] / max(1e-9, hp["host_copy_ms"] / 1e3)
+                                             / 1e9, 1),
+                    "kernel_ms_device_resident": round(kernel_ms * B / (rows_done / launches), 2)}
         e2e = {"value": pairs * rows_e2e / te, "unit": UNIT,
                "h2d_bytes_per_step": int(host_matrix_bytes(n) + B * n + K * 4),
                "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps, "step_ms": step_ms,
-               "clocks": e2e_clocks, "h2d_gbs": round(h2d_gbs, 1),
+               "clocks": e2e_clocks, "h2d_gbs": round(h2d_gbs, 1), "h2d_gbs_at_offsets": h2d_at,
+               "timeline": timeline,
                "api": "permanova_sW_host (pinned host D, labels, weights, results; "
                       "copies D's band trapezoids in segments overlapped with the kernels)"}
 

@@ -173,7 +173,9 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
  * gives full copy speed).  The call copies the inputs to the device, runs
  * s_W, copies the n_perms results back and synchronises `stream`.  Only the
  * part of mat that s_W reads is copied: for each 128-row band, rows
- * [128 b, 128 b + 128) from column 128 b on (about half of the matrix).  The
+ * [128 b, 128 b + 128) from column 128 b on (about half of the matrix); with
+ * the tensor-core form only those band trapezoids are staged on the device
+ * (context scratch of about half the matrix), else a full-width copy.  The
  * copies run on a stream of the context, ordered after the work already queued
  * on `stream`; with the tensor-core form the bands are copied in up to 16
  * segments and each segment's kernels start as soon as it has landed, so the
@@ -188,9 +190,10 @@ int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uin
 
 /* permanova_sW for callers that cannot allocate device memory.  The paper has
  * no counterpart: this is a deployment variant.  Callers that cannot call
- * cudaMalloc include code recording a CUDA graph that must not contain
- * allocations, plugins whose host framework owns every device allocation,
- * and processes pinned to a fixed memory pool with no headroom.
+ * cudaMalloc include plugins whose host framework owns every device
+ * allocation (and forbids others), and processes confined to a fixed device
+ * memory pool with no headroom, where a new allocation would fail or evict
+ * the host framework's own buffers.
  * It needs no context and allocates nothing: it runs the brute-force kernels
  * with their scratch (FP64 partial sums, FP64 weights, the device error word)
  * in one fixed 8 MiB device array that the library keeps resident on every
@@ -200,12 +203,15 @@ int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uin
  *   Limits: n_perms * 8 bytes must fit in the array after the error word and
  *   the weights (1,048,512 label rows with n_groups <= 32); larger calls
  *   return PERMANOVA_EINVAL with a message, before any work is queued.
- *   The first call on a device looks up the array's device address; make
- *   that first call outside any stream capture.
+ *   Set-up: the first call on a device (and the first after the device's
+ *   context was replaced, e.g. by cudaDeviceReset) looks up the array's
+ *   device address; make that call before any stream capture on the device.
  *   The call synchronises `stream` and reports a label >= n_groups as
- *   PERMANOVA_EINVAL.  All calls on a device share the array: calls whose work
- *   overlaps on the GPU (other streams, other host threads) race, so callers
- *   must serialise them.  Error text: permanova_last_error(NULL). */
+ *   PERMANOVA_EINVAL.  All calls on a device share the array, and it keeps
+ *   the last call's contents (each call clears the error word and overwrites
+ *   the weights and partials it reads): calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race, so callers must serialise
+ *   them.  Error text: permanova_last_error(NULL). */
 int permanova_sW_noalloc(const float *mat, uint32_t n_dims, uint64_t ld, const void *groupings,
                          int label_type, uint32_t n_groups, uint64_t n_perms,
                          const float *inv_group_sizes, double *out_sW, void *stream);
@@ -232,14 +238,22 @@ int permanova_permutations(permanova_ctx *ctx, const int32_t *grouping, uint32_t
                            int label_type, void *stream);
 
 /* Profiling counters of a context (not a paper operation; measurement
- * support).  While enabled, every s_W call records CUDA events on its stream
- * around its dominant kernel (the brute-force, perm-block or GEMM kernel) and
- * every kernel the library launches is counted. */
+ * support).  While enabled, every s_W call on device buffers records CUDA
+ * events on its stream around its dominant kernel (the brute-force, perm-block
+ * or GEMM kernel), every kernel the library launches is counted, and every
+ * permanova_sW_host call records events at its start, when the first and the
+ * last segment of the matrix have landed on the device, and at its end (the
+ * results copied back). */
 typedef struct {
     double main_kernel_ms;          /* summed event time of the dominant kernels */
     uint64_t main_kernel_launches;  /* dominant-kernel launches recorded */
     uint64_t kernel_launches;       /* all kernels launched by the library */
     int last_form;                  /* permanova_form_t of the last s_W call */
+    uint64_t host_calls;            /* permanova_sW_host calls recorded */
+    double host_total_ms;           /* summed device time, call start to results copied back */
+    double host_first_segment_ms;   /* summed time until the first matrix segment landed */
+    double host_copy_ms;            /* summed time until the last matrix segment landed */
+    uint64_t host_h2d_bytes;        /* bytes those calls copied host to device */
 } permanova_profile_t;
 
 /* Enable (1) or disable (0) profiling; enabling clears the counters. */

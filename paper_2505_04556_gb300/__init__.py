@@ -48,7 +48,10 @@ class permanova_result(ctypes.Structure):
 
 class permanova_profile_t(ctypes.Structure):
     _fields_ = [("main_kernel_ms", ctypes.c_double), ("main_kernel_launches", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64), ("last_form", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_uint64), ("last_form", ctypes.c_int),
+                ("host_calls", ctypes.c_uint64), ("host_total_ms", ctypes.c_double),
+                ("host_first_segment_ms", ctypes.c_double), ("host_copy_ms", ctypes.c_double),
+                ("host_h2d_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -249,8 +252,10 @@ def permanova_set_graphs(ctx, enable: bool = True) -> None:
 
 def permanova_sW_noalloc(mat, n_dims: int, ld: int, groupings, label_type: int, n_groups: int,
                          n_perms: int, inv_group_sizes, out_sW, stream=None) -> None:
-    """s_W with no device allocation (fixed 8 MiB library-resident scratch; for
-    callers that must not call cudaMalloc).  Synchronises the stream."""
+    """s_W with no device allocation: the scratch is a fixed 8 MiB array that
+    the library keeps resident on the device, for callers that may not call
+    cudaMalloc (plugins of frameworks that own all device memory, processes
+    in a fixed memory pool).  Synchronises the stream."""
     rc = load().permanova_sW_noalloc(_ptr(mat), int(n_dims), int(ld), _ptr(groupings),
                                      int(label_type), int(n_groups), int(n_perms),
                                      _ptr(inv_group_sizes), _ptr(out_sW), _stream(stream))

@@ -62,7 +62,34 @@ struct SWProblem {
     // Weight sets: 0 = one set of K weights for every label row; otherwise
     // label row p uses w[(p / w_set_rows) * K + g] (several tests in one pass).
     uint64_t w_set_rows;
+    // Layout of mat: 0 = row-major with row stride ld; 1 = band trapezoids
+    // (see band_trapezoid_offset; tensor-core form only, ld unused).
+    uint32_t banded;
 };
+
+// Band-trapezoid layout of the strict upper triangle (the host entry point's
+// staging of D for the tensor-core form): band I holds rows [128 I, 128 I + 128)
+// from column 128 I on, with row stride n4 - 128 I (n4 = n rounded up to 4),
+// bands stored back to back.  Offset (in floats) of band I's first element:
+// 128 * sum_{I' < I} (n4 - 128 I').
+__host__ __device__ __forceinline__ uint64_t band_trapezoid_offset(uint64_t I, uint64_t n4) {
+    return 128ull * (I * n4 - (I ? 64ull * I * (I - 1) : 0ull));
+}
+// Total floats of the layout for n objects.
+__host__ __device__ __forceinline__ uint64_t band_trapezoid_floats(uint32_t n) {
+    const uint64_t n4 = (n + 3ull) / 4 * 4, nb = (n + 127ull) / 128, last = nb - 1;
+    const uint64_t rows_last = n - 128ull * last;
+    return band_trapezoid_offset(last, n4) + rows_last * (n4 - 128ull * last);
+}
+// Address of element (i, 0) of row i in either layout (only elements j >=
+// 128 * (i / 128) of a band-trapezoid row exist; the address itself may lie
+// before the row's first stored element).
+__host__ __device__ __forceinline__ const float* d_row(const float* mat, uint64_t ld, uint32_t banded,
+                                                       uint32_t n, uint32_t i) {
+    if (!banded) return mat + (uint64_t)i * ld;
+    const uint64_t n4 = (n + 3ull) / 4 * 4, I = i >> 7;
+    return mat + band_trapezoid_offset(I, n4) + (uint64_t)(i - 128 * I) * (n4 - 128 * I) - 128 * I;
+}
 
 // Weight of group g for label row p.
 __host__ __device__ __forceinline__ const double* weight_row(const double* w, uint64_t p,

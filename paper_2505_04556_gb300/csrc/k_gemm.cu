@@ -325,12 +325,15 @@ __device__ __forceinline__ void tile_coords(uint64_t t, uint32_t n_bands, uint32
 }
 
 // d^2 of the 8 entries (i, j0 .. j0+7) in FP32, zero outside the strict upper
-// triangle (j <= i, i >= n or j >= n).
-__device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t n, uint64_t ld, bool vec,
-                                         bool diag, uint32_t i, uint32_t j0, float (&x)[8]) {
+// triangle (j <= i, i >= n or j >= n).  D is row-major (stride ld) or in the
+// band-trapezoid layout (banded); j0 >= 128 * (i / 128) in both.
+__device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t n, uint64_t ld,
+                                         uint32_t banded, bool vec, bool diag, uint32_t i, uint32_t j0,
+                                         float (&x)[8]) {
     float v[8];
+    const float* row = i < n ? d_row(mat, ld, banded, n, i) : mat;
     if (i < n && vec && !diag && j0 + 7 < n) {
-        const float4* src = reinterpret_cast<const float4*>(mat + (uint64_t)i * ld + j0);
+        const float4* src = reinterpret_cast<const float4*>(row + j0);
         const float4 a = __ldg(src), b = __ldg(src + 1);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
@@ -339,7 +342,7 @@ __device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t
         for (int e = 0; e < 8; ++e) {
             const uint32_t j = j0 + e;
             v[e] = 0.f;
-            if (i < n && j < n && j > i) v[e] = __ldg(mat + (uint64_t)i * ld + j);
+            if (i < n && j < n && j > i) v[e] = __ldg(row + j);
         }
     }
 #pragma unroll
@@ -353,7 +356,7 @@ __device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t
 // non-negative floats (bit order = value order), into bmax[I] (zeroed
 // beforehand) and bmin[I] (set to all ones beforehand).
 __global__ void __launch_bounds__(256)
-k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
+k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t n_bands, bool vec,
                 uint64_t t0, uint64_t t1, uint32_t* __restrict__ bmax, uint32_t* __restrict__ bmin) {
     __shared__ uint32_t wmax[8], wmin[8];
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
@@ -363,7 +366,7 @@ k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t
         uint32_t m = 0, mn = 0xFFFFFFFFu;
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             float x[8];
-            squared8(mat, n, ld, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
+            squared8(mat, n, ld, banded, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const uint32_t b = __float_as_uint(x[e]);
@@ -393,7 +396,7 @@ k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t
 }
 
 __global__ void __launch_bounds__(256)
-k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_bands, bool vec,
+k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t n_bands, bool vec,
             uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles, const uint32_t* __restrict__ bmax,
             const uint32_t* __restrict__ bmin) {
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
@@ -406,7 +409,7 @@ k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t n_b
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             const uint32_t r = job >> 3, c8 = job & 7;
             float x[8];
-            squared8(mat, n, ld, vec, diag, I * g::BM + r, kb * g::BK + c8 * 8, x);
+            squared8(mat, n, ld, banded, vec, diag, I * g::BM + r, kb * g::BK + c8 * 8, x);
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
@@ -433,7 +436,9 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
                              uint32_t I0, uint32_t I1) {
     if (I1 > gp.n_bands) I1 = gp.n_bands;
     if (I0 >= I1) return cudaSuccess;
-    const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
+    // a band-trapezoid D has 16-byte aligned rows (every offset and stride a
+    // multiple of 4 floats) whenever its base is
+    const bool vec = (pr.banded || pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
     const uint64_t NB = 2ull * gp.n_bands;
     const uint64_t t0 = tiles_before_band(I0, NB), t1 = tiles_before_band(I1, NB);
     const uint64_t n_tiles = t1 - t0;
@@ -444,8 +449,8 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
     cudaError_t e = cudaMemsetAsync(bmax + I0, 0, (size_t)(I1 - I0) * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bmin + I0, 0xFF, (size_t)(I1 - I0) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, bmax, bmin);
-    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, gp.n_bands, vec, t0, t1, tiles, bmax, bmin);
+    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, gp.n_bands, vec, t0, t1, bmax, bmin);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, gp.n_bands, vec, t0, t1, tiles, bmax, bmin);
     return launched(2);
 }
 

@@ -1,9 +1,9 @@
 // s_W without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA stream
-// capture that must not add allocation nodes, plugins of host frameworks that
-// own every device allocation themselves (and forbid others), and processes
-// that run with a fixed memory pool and no headroom.  For them,
+// Some callers cannot call cudaMalloc: plugins of host frameworks that own
+// every device allocation themselves (and forbid others), and processes that
+// run inside a fixed device-memory pool with no headroom, where a fresh
+// allocation would fail or evict the framework's own buffers.  For them,
 // permanova_sW_noalloc runs the brute-force s_W kernels with their scratch
 // (FP64 partial sums, FP64 weights, the device error word) in one fixed
 // file-scope device array instead of context memory.  It needs no context.
@@ -13,8 +13,17 @@
 // it, so calls whose work overlaps on that GPU (different streams or host
 // threads) race; callers must serialise them.  Each call clears the error
 // word before use and overwrites the partials and weights it reads.
+//
+// Host code cannot use the array's name as an address (in host code it names
+// a host-side stand-in), so the device address is looked up with
+// cudaGetSymbolAddress at set-up: on the first call on a device, with that
+// device current, and again whenever the device's context has been replaced
+// (after a cudaDeviceReset, say), which the cache detects through the
+// context's process-unique ID.
 #include "../../include/permanova.h"
 #include "common.cuh"
+
+#include <cuda.h>
 
 #include <cstdio>
 #include <mutex>
@@ -30,21 +39,63 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;   // process-unique ID of the context the address belongs to
+    void* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES];
+// driver entry points (signatures of cuCtxGetCurrent and cuCtxGetId), found
+// through the runtime so the library needs no link against the driver
+using CtxCurrentFn = CUresult (*)(CUcontext*);
+using CtxIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxCurrentFn g_ctx_current = nullptr;
+CtxIdFn g_ctx_id = nullptr;
+
+// Process-unique ID of the calling thread's current context (0 if none).
+cudaError_t current_context_id(unsigned long long* id) {
+    *id = 0;
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        g_ctx_current = reinterpret_cast<CtxCurrentFn>(f1);
+        g_ctx_id = reinterpret_cast<CtxIdFn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_current(&c) != CUDA_SUCCESS || c == nullptr) return cudaErrorDeviceUninitialized;
+    if (g_ctx_id(c, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 }  // namespace
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the first call on a device must therefore not be inside a
-// stream capture).
+// Device address of the scratch array on the current device.  Set-up runs on
+// the first call on a device (and after the device's context was replaced):
+// it makes sure the device's primary context exists, then looks the address
+// up; that call must therefore come before any stream capture on the device.
 static cudaError_t noalloc_base(int dev, void** out) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    // selecting the (already current) device initialises its primary context
+    // if that has not happened yet, so the context below exists
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return e;
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    if (slot.ptr == nullptr || slot.ctx_id != id) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return cudaSuccess;
 }
 
@@ -88,7 +139,7 @@ extern "C" int permanova_sW_noalloc(const float* mat, uint32_t n, uint64_t ld, c
     void* base = nullptr;
     cudaError_t e = noalloc_base(dev, &base);
     if (e != cudaSuccess) {
-        snprintf(msg, sizeof msg, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        snprintf(msg, sizeof msg, "no-allocation scratch set-up: %s", cudaGetErrorString(e));
         return err(PERMANOVA_ECUDA, msg);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -5,6 +5,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +52,10 @@ struct permanova_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     uint64_t launch_mark = 0;
     int last_form = 0;
+    // host entry point (profiling): per call, timing events at its start, when
+    // the first and the last matrix segment have landed, and at its end
+    std::vector<std::array<cudaEvent_t, 4>> host_events;
+    uint64_t host_h2d_bytes = 0;
     // host entry point: copies run on their own stream, ordered by events;
     // matrix segments alternate between the caller's stream and seg_stream so
     // that one segment's last wave overlaps the next segment's first
@@ -121,10 +126,10 @@ int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
     if (ctx->forced_form != PERMANOVA_FORM_AUTO) return ctx->forced_form;
     auto it = ctx->tuned.find(TuneKey{log2_bucket(n), K, log2_bucket(P)});
     if (it != ctx->tuned.end()) return it->second;
-    // The tensor-core form costs 4K flops per pair and label row (two BF16
+    // The tensor-core form costs 4K flops per pair and label row (two 16-bit
     // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
     // Measured on a GB300 at n = 20,000 with 4,000 label rows: the GEMM form is
-    // 2.5x the perm-block form at K = 16, 1.27x at K = 32 and 0.96x at K = 40.
+    // 2.22x the perm-block form at K = 16, 1.11x at K = 32 and 0.85x at K = 40.
     if (gemm_available() && K <= 32 && n >= 256 && P >= 32) return PERMANOVA_FORM_GEMM;
     if (P >= 16 && K <= 65536) return PERMANOVA_FORM_PERMBLOCK;
     return PERMANOVA_FORM_BRUTE;
@@ -249,6 +254,10 @@ void profile_clear(permanova_ctx* ctx) {
         cudaEventDestroy(e.second);
     }
     ctx->events.clear();
+    for (auto& h : ctx->host_events)
+        for (cudaEvent_t e : h) cudaEventDestroy(e);
+    ctx->host_events.clear();
+    ctx->host_h2d_bytes = 0;
     ctx->launch_mark = kernel_launch_count();
 }
 
@@ -543,9 +552,12 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
     const int forms[3] = {PERMANOVA_FORM_BRUTE, PERMANOVA_FORM_PERMBLOCK, PERMANOVA_FORM_GEMM};
     double best_t = 1e300;
     int best = PERMANOVA_FORM_BRUTE;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
-    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    if (cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
     for (int form : forms) {
         // the brute force re-reads D per label row: skip it where it cannot win
         if (form == PERMANOVA_FORM_BRUTE && Ps > 64 && pairs * Ps > 4e11) continue;
@@ -599,6 +611,18 @@ int permanova_profile_read(permanova_ctx* ctx, permanova_profile_t* out) {
     }
     out->main_kernel_ms = ms;
     out->main_kernel_launches = ctx->events.size();
+    out->host_calls = ctx->host_events.size();
+    out->host_total_ms = out->host_first_segment_ms = out->host_copy_ms = 0.0;
+    for (auto& h : ctx->host_events) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        CK(cudaEventElapsedTime(&a, h[0], h[1]), "cudaEventElapsedTime");
+        CK(cudaEventElapsedTime(&b, h[0], h[2]), "cudaEventElapsedTime");
+        CK(cudaEventElapsedTime(&c, h[0], h[3]), "cudaEventElapsedTime");
+        out->host_first_segment_ms += a;
+        out->host_copy_ms += b;
+        out->host_total_ms += c;
+    }
+    out->host_h2d_bytes = ctx->host_h2d_bytes;
     out->kernel_launches = kernel_launch_count() - ctx->launch_mark;
     out->last_form = ctx->last_form;
     profile_clear(ctx);
@@ -624,10 +648,14 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     SWLayout L;
     rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
     if (rc) return rc;
-    // staging for the inputs and the output after the s_W scratch; the staged
-    // matrix has a row stride of n rounded up to 4 floats (16-byte rows)
-    const uint64_t ldd = (n + 3ull) / 4 * 4;
-    const size_t mat_bytes = (size_t)n * ldd * sizeof(float);
+    // staging for the inputs and the output after the s_W scratch.  The
+    // tensor-core form reads D only through its band trapezoids, so it stages
+    // just those (band I: rows [128 I, 128 I + 128) from column 128 I on, row
+    // stride n4 - 128 I, about half of the matrix); the CUDA-core forms get a
+    // full copy with rows of n4 floats (n4 = n rounded up to 4: 16-byte rows).
+    const bool banded = L.form == PERMANOVA_FORM_GEMM;
+    const uint64_t n4 = (n + 3ull) / 4 * 4;
+    const size_t mat_bytes = (banded ? (size_t)band_trapezoid_floats(n) : (size_t)n * n4) * sizeof(float);
     const size_t lab_bytes = (size_t)n * P * label_bytes(label_type);
     size_t off = L.total;
     const size_t mat_off = off;
@@ -661,6 +689,20 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create copy event");
         ctx->copy_events.push_back(e);
     }
+    // profiling: timing events at the start, first segment, last segment, end
+    std::array<cudaEvent_t, 4> tev{};
+    if (ctx->profiling) {
+        for (auto& e : tev) {
+            if (cudaError_t ce = cudaEventCreate(&e); ce != cudaSuccess) {
+                for (cudaEvent_t x : tev)
+                    if (x) cudaEventDestroy(x);
+                return cuda_fail(ce, "cudaEventCreate");
+            }
+        }
+        ctx->host_events.push_back(tev);
+        ctx->host_h2d_bytes += lab_bytes + (size_t)K * sizeof(float);
+        CK(cudaEventRecord(tev[0], s), "record start");
+    }
     cudaStream_t cs = ctx->copy_stream;
     Arrival arr;
     arr.lab_ready = ctx->copy_events[0];
@@ -686,28 +728,34 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     float* dmat = reinterpret_cast<float*>(base + mat_off);
     for (uint32_t I = 0; I < n_bands; ++I) {
         const uint32_t r0 = 128 * I, r1 = std::min(n, r0 + 128);
-        CK(cudaMemcpy2DAsync(dmat + (uint64_t)r0 * ldd + r0, ldd * sizeof(float), mat + (uint64_t)r0 * ld + r0,
-                             ld * sizeof(float), (size_t)(n - r0) * sizeof(float), r1 - r0,
-                             cudaMemcpyHostToDevice, cs),
+        float* dst = banded ? dmat + band_trapezoid_offset(I, n4) : dmat + (uint64_t)r0 * n4 + r0;
+        const uint64_t dpitch = banded ? n4 - 128ull * I : n4;
+        CK(cudaMemcpy2DAsync(dst, dpitch * sizeof(float), mat + (uint64_t)r0 * ld + r0, ld * sizeof(float),
+                             (size_t)(n - r0) * sizeof(float), r1 - r0, cudaMemcpyHostToDevice, cs),
            "copy matrix band");
+        if (ctx->profiling) ctx->host_h2d_bytes += (size_t)(n - r0) * sizeof(float) * (r1 - r0);
         acc += band_area(I);
         const size_t k = arr.band.size() - 1;   // segment being filled
         if (I + 1 == n_bands || acc >= total * (double)(k + 1) / n_seg) {
             cudaEvent_t e = ctx->copy_events[2 + k];
             CK(cudaEventRecord(e, cs), "record segment");
+            if (ctx->profiling && k == 0) CK(cudaEventRecord(tev[1], cs), "record first segment");
             arr.seg_ready.push_back(e);
             arr.band.push_back(I + 1);
         }
     }
+    if (ctx->profiling) CK(cudaEventRecord(tev[2], cs), "record last segment");
     // the staged label buffer is 256-byte aligned: re-plan so the direct path can be taken
-    rc = layout_for(ctx, L.form, n, ldd, base + lab_off, label_type, K, P, &L);
+    rc = layout_for(ctx, L.form, n, n4, base + lab_off, label_type, K, P, &L);
     if (rc) return rc;
-    SWProblem pr{reinterpret_cast<const float*>(dmat), n, ldd, base + lab_off, label_type, K,
+    SWProblem pr{reinterpret_cast<const float*>(dmat), n, n4, base + lab_off, label_type, K,
                  P, nullptr, reinterpret_cast<double*>(base + out_off)};
+    pr.banded = banded ? 1u : 0u;
     rc = run_sW(ctx, L, pr, reinterpret_cast<const float*>(base + w_off), s, &arr);
     if (rc) return rc;
     CK(cudaMemcpyAsync(out, base + out_off, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, s),
        "copy results");
+    if (ctx->profiling) CK(cudaEventRecord(tev[3], s), "record end");
     return read_status(ctx, s);
 }
 

@@ -65,7 +65,7 @@ def test_cuda_path_matches_golden():
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), np.array(_rows("permutations_n37.txt"), dtype=np.int32))
         want = np.array([float.fromhex(r[0]) for r in _rows("sW_integer_n16.txt")])
-        for form in (pm.FORM_BRUTE, pm.FORM_PERMBLOCK):
+        for form in (pm.FORM_BRUTE, pm.FORM_PERMBLOCK, pm.FORM_GEMM, pm.FORM_AUTO):
             ctx.set_form(form)
             got = ctx.sW(torch.from_numpy(D16).cuda(), torch.from_numpy(rows16).cuda(), 3,
                          torch.from_numpy(synth.inv_sizes(lab16, 3)).cuda())

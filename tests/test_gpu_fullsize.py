@@ -3,7 +3,10 @@ times (default kernel plan, uint8 label rows, the benchmark's batch sizes).
 
 * n = 1,000 / 999 rows and n = 20,000 / 3,999 rows: sampled rows against the
   FP64 oracle (Algorithm 1) one by one.
-* n = 50,000 Bray-Curtis / 8,192 rows: sampled rows against the oracle.
+* n = 50,000 Bray-Curtis / 8,192 rows: 64 rows spread over the launch (both
+  ends, every label-row tile position in between) against the oracle.
+* n = 25,145 Jaccard / 4,000 rows (the paper's own workload shape, Sec. 3):
+  64 sampled rows against the oracle.
 * n = 100,000 / 8,192 rows (the headline workload): 512 rows spread over
   the launch against Huygens' identity for Euclidean distances, s_W =
   sum_g sum_{i in g} |x_i - mu_g|^2 computed from the generating points in
@@ -59,11 +62,34 @@ def test_full_size_sampled_rows(ctx, name, n_rows, sample):
     np.testing.assert_allclose(got[idx], ref, rtol=RTOL)
 
 
+def _spread(n_rows, count):
+    """``count`` label rows spread over a launch: both ends, the first and last
+    rows of several label-row tiles, and evenly spaced rows in between."""
+    idx = {0, 1, 24, 25, 127, 128, n_rows - 2, n_rows - 1}
+    idx.update(int(round(k * (n_rows - 1) / (count - 1))) for k in range(count))
+    k = 3
+    while len(idx) < count:           # fill up with odd offsets if rounding collided
+        idx.add((k * 7919) % n_rows)
+        k += 1
+    return np.array(sorted(idx))
+
+
 def test_full_size_braycurtis_50k(ctx):
     cfg = synth.recipe("braycurtis-50k")
     X = synth.recipe_points(cfg)
     D, lab, got = _run(ctx, cfg, X, 8192, 32)
-    idx = np.array([0, 1, 4095, 8191])
+    idx = _spread(8192, 64)
+    assert len(idx) >= 64
+    ref = _oracle_rows(D, lab, cfg, idx)
+    np.testing.assert_allclose(got[idx], ref, rtol=RTOL)
+
+
+def test_full_size_jaccard_25k(ctx):
+    cfg = synth.recipe("jaccard-25k")
+    X = synth.recipe_points(cfg)
+    D, lab, got = _run(ctx, cfg, X, 4000, 34)
+    idx = _spread(4000, 64)
+    assert len(idx) >= 64
     ref = _oracle_rows(D, lab, cfg, idx)
     np.testing.assert_allclose(got[idx], ref, rtol=RTOL)
 

@@ -120,17 +120,24 @@ def test_many_groups(ctx, form, K, ltype):
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-12)
 
 
-@pytest.mark.parametrize("form", FORMS[:2])
-def test_integer_matrix_bit_exact(ctx, form):
-    # entries in 0..15, groups 64/32/32: every partial sum is exact in FP32/FP64
-    n = 128
-    D = synth.integer_matrix(n, 15, 5)
-    obs = synth.observed_labels([64, 32, 32], 6)
-    rows = synth.shuffled_rows(obs, 33, 7)
-    w = synth.inv_sizes(obs, 3)
-    ref = oracle.sW_alg1(D, rows, 3, w.astype(np.float64))
-    got = _run_sW(ctx, D, rows, 3, w, form)
-    assert np.array_equal(got, ref)
+@pytest.mark.parametrize("form", FORMS + [pytest.param(pm.FORM_AUTO, id="auto")])
+@pytest.mark.parametrize("n,sizes", [(128, [64, 32, 32]), (1001, [512, 256, 128, 64, 41]),
+                                     (4096, [2048, 1024, 1024])])
+def test_integer_matrix_bit_exact(ctx, form, n, sizes):
+    """Integer entries 0..15 with power-of-two weights: every sum of every form
+    is exact, so every form equals the FP64 oracle bit for bit.  For the
+    tensor-core form the bound is: d^2 <= 255 fits the BF16 hi plane exactly
+    (the lo plane is 0), the band scale is a power of two, and the largest FP32
+    sum it forms (32 rows x 2,048 columns of one label-row column before the
+    FP64 hand-off) stays below 2^24 band units, so no FP32 step rounds."""
+    D = synth.integer_matrix(n, 15, 5 + n)
+    K = len(sizes)
+    obs = synth.observed_labels(sizes, 6 + n)
+    rows = synth.shuffled_rows(obs, 33, 7 + n)
+    w = np.array([2.0 ** -(k + 3) for k in range(K)], dtype=np.float32)   # exact weights
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    got = _run_sW(ctx, D, rows, K, w, form, pm.LABEL_U8)
+    assert np.array_equal(got, ref), np.max(np.abs(got - ref) / ref)
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -392,3 +399,30 @@ def test_host_entry_segments(ctx, form, n, ld):
     idx = np.arange(0, P, 7)
     ref = oracle.sW_alg1(D, rows[idx], K, w.astype(np.float64))
     np.testing.assert_allclose(out[idx], ref, rtol=RTOL)
+
+
+def test_host_entry_profile(ctx):
+    """With profiling on, the host entry point records one call, the bytes it
+    copied (the band trapezoids of D, the labels and the weights) and an
+    ordered device timeline: first segment <= last segment <= end."""
+    n, ld, K, P = 1000, 1003, 5, 70
+    D, rows, w = _case(n, K, P, seed=41)
+    Dp = np.zeros((n, ld), dtype=np.float32)
+    Dp[:, :n] = D
+    lab = np.ascontiguousarray(rows.astype(np.uint8))
+    out = np.zeros(P, dtype=np.float64)
+    ctx.set_form(pm.FORM_GEMM)
+    try:
+        pm.permanova_profile_enable(ctx.handle, True)
+        pm.permanova_sW_host(ctx.handle, Dp, n, ld, lab, pm.LABEL_U8, K, P,
+                             np.ascontiguousarray(w, dtype=np.float32), out)
+        prof = pm.permanova_profile_read(ctx.handle)
+    finally:
+        pm.permanova_profile_enable(ctx.handle, False)
+        ctx.set_form(pm.FORM_AUTO)
+    trap = sum(min(128, n - r0) * (n - r0) * 4 for r0 in range(0, n, 128))
+    assert prof["host_calls"] == 1
+    assert prof["host_h2d_bytes"] == trap + n * P + 4 * K
+    assert 0.0 < prof["host_first_segment_ms"] <= prof["host_copy_ms"] <= prof["host_total_ms"]
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    np.testing.assert_allclose(out, ref, rtol=RTOL)

@@ -1,14 +1,18 @@
-"""permanova_sW_noalloc: s_W for callers that cannot allocate device memory
-(graph capture without allocation nodes, frameworks that own every device
-allocation, fixed memory pools).  It runs with the library's fixed resident
-scratch array and must give the same s_W as permanova_sW, call after call.
+"""permanova_sW_noalloc: s_W for callers that may not allocate device memory
+(plugins of frameworks that own every device allocation, processes confined
+to a fixed memory pool).  It runs with the library's fixed resident scratch
+array and must give the same s_W as permanova_sW and as the FP64 oracle, call
+after call, although every call reuses (and overwrites) the same array.
 
 This file is collected last so that a failure here cannot hide any other
-test's result in a run that stops at the first failure.
+test's result in a run that stops at the first failure.  It passes alone in a
+fresh process (the first call on the device does the array's set-up) and
+after the other tests.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -36,26 +40,35 @@ def _case(n, K, P, seed):
     sizes = synth.largest_remainder_sizes(n, rng.dirichlet(2 * np.ones(K)), min_size=1)
     obs = synth.observed_labels(sizes, seed + 1)
     rows = synth.shuffled_rows(obs, P, seed + 2)
-    return (torch.from_numpy(D).cuda(), torch.from_numpy(rows.astype(np.uint8)).cuda(),
-            torch.from_numpy(synth.inv_sizes(obs, K)).cuda())
+    w = synth.inv_sizes(obs, K)
+    return D, rows, w
 
 
-def test_noalloc_matches_permanova_sW_twice(ctx):
-    for n, K, P, seed in ((1001, 4, 37, 1), (257, 3, 300, 2)):
-        D, lab, w = _case(n, K, P, seed)
-        ref = torch.empty(P, dtype=torch.float64, device="cuda")
-        pm.permanova_sW(ctx.handle, D, n, n, lab, pm.LABEL_U8, K, P, w, ref)
-        pm.permanova_sync(ctx.handle)
-        for _ in range(2):   # two calls in a row share (and reuse) the same scratch
-            out = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
-            pm.permanova_sW_noalloc(D, n, n, lab, pm.LABEL_U8, K, P, w, out)
-            np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=RTOL)
+@pytest.mark.parametrize("n,K,P,seed", [(1001, 4, 37, 1), (257, 3, 300, 2), (130, 7, 5, 4)])
+def test_noalloc_matches_permanova_sW_and_oracle_twice(ctx, n, K, P, seed):
+    D, rows, w = _case(n, K, P, seed)
+    ref_oracle = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    Dd = torch.from_numpy(D).cuda()
+    lab = torch.from_numpy(rows.astype(np.uint8)).cuda()
+    wd = torch.from_numpy(w).cuda()
+    ref = torch.empty(P, dtype=torch.float64, device="cuda")
+    pm.permanova_sW(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd, ref)
+    pm.permanova_sync(ctx.handle)
+    ref = ref.cpu().numpy()
+    for _ in range(2):   # two calls in a row share (and reuse) the same scratch
+        out = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
+        pm.permanova_sW_noalloc(Dd, n, n, lab, pm.LABEL_U8, K, P, wd, out)
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=RTOL)
+        np.testing.assert_allclose(got, ref_oracle, rtol=RTOL)
 
 
 def test_noalloc_rejects_oversized_calls(ctx):
-    D, lab, w = _case(64, 2, 4, 3)
+    D, rows, w = _case(64, 2, 4, 3)
     out = torch.empty(4, dtype=torch.float64, device="cuda")
     with pytest.raises(pm.PermanovaError) as ei:
-        pm.permanova_sW_noalloc(D, 64, 64, lab, pm.LABEL_U8, 2, 2_000_000, w, out)
+        pm.permanova_sW_noalloc(torch.from_numpy(D).cuda(), 64, 64,
+                                torch.from_numpy(rows.astype(np.uint8)).cuda(), pm.LABEL_U8, 2,
+                                2_000_000, torch.from_numpy(w).cuda(), out)
     assert ei.value.status == pm.EINVAL
     assert "no-allocation scratch" in str(ei.value)

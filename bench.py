@@ -283,18 +283,20 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
-def serving_bench(args) -> None:
+def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
+                seed: int = 5005) -> dict:
     """Serving workload: 64 resident matrices (n log-uniform in 500..30,000,
     Gaussian points in R^16/R^32, Euclidean fp32), each with 1-20 categorical
     factors (K uniform in 2..12, Dirichlet(2) sizes, each group >= 2), tests of
     999 or 9,999 permutations (even odds) arriving as a Poisson process at
-    ``--rate`` tests/s for ``--duration`` seconds.  Prints tests/s and p50/p99
-    latency (arrival to result)."""
+    ``rate`` tests/s.  Arrivals during the first ``warmup_s`` seconds are
+    served but not counted; tests/s and p50/p99 latency (arrival to result)
+    are taken over the ``duration`` seconds after that."""
     import torch
     import paper_2505_04556_gb300 as pm
     from paper_2505_04556_gb300.serve import Request, Server
     pm.build()
-    rng = np.random.default_rng(5005)
+    rng = np.random.default_rng(seed)
     mats, factors = {}, {}
     for m in range(64):
         n = int(round(math.exp(rng.uniform(math.log(500), math.log(30000)))))
@@ -309,46 +311,63 @@ def serving_bench(args) -> None:
             fl.append((synth.observed_labels(sizes, int(rng.integers(1 << 30))), K))
         factors[m] = fl
     torch.cuda.synchronize()
-    srv = Server(mats, n_slots=args.slots)
-    reqs = []
+    resident = sum(int(D.numel()) * 4 for D in mats.values())
+    srv = Server(mats, n_slots=slots, reserve_per_slot=8 << 30)
+    reqs, measured = [], []
     t0 = time.perf_counter()
     t_next = t0
     k = 0
     while True:
-        t_next += rng.exponential(1.0 / args.rate)
-        if t_next - t0 > args.duration:
+        t_next += rng.exponential(1.0 / rate)
+        if t_next - t0 > warmup_s + duration:
             break
         while time.perf_counter() < t_next:
             time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
         m = int(rng.integers(64))
         lab, K = factors[m][int(rng.integers(len(factors[m])))]
         P = 999 if rng.random() < 0.5 else 9999
-        reqs.append(srv.submit(Request(m, lab, K, P, seed=10_000 + k)))
+        r = srv.submit(Request(m, lab, K, P, seed=10_000 + k))
+        reqs.append(r)
+        if t_next - t0 >= warmup_s:
+            measured.append(r)
         k += 1
     for r in reqs:
         r.done.wait(600)
-    wall = max(r.t_done for r in reqs) - t0
+    t_meas = t0 + warmup_s
+    wall = max(r.t_done for r in measured) - t_meas
     srv.close()
-    s = Server.summarize(reqs, wall)
+    s = Server.summarize(measured, wall)
     evals = sum(mats[r.matrix_id].shape[0] * (mats[r.matrix_id].shape[0] - 1) / 2 * (r.n_perms + 1)
-                for r in reqs if r.error is None)
-    line = {"metric": "served PERMANOVA tests/s (p50/p99 latency)", "value": s.get("tests_per_s"),
-            "unit": "tests/s", "p50_s": s.get("p50_s"), "p99_s": s.get("p99_s"),
-            "tests": s.get("tests"), "errors": s.get("errors"), "offered_rate": args.rate,
-            "duration_s": args.duration, "slots": args.slots,
-            "pair_perm_evals_per_s": evals / wall, "higher_is_better": True, "n_gpus": 1,
-            "data": "synthetic",
-            "config": {"workload": "serving-64", "matrices": 64, "n_range": [500, 30000],
-                       "perms": [999, 9999], "K_range": [2, 12], "arrivals": "Poisson"},
-            "gpu": torch.cuda.get_device_name(0)}
+                for r in measured if r.error is None)
+    out = {"metric": "served PERMANOVA tests/s (p50/p99 latency)", "value": s.get("tests_per_s"),
+           "unit": "tests/s", "p50_s": s.get("p50_s"), "p99_s": s.get("p99_s"),
+           "tests": s.get("tests"), "errors": s.get("errors"), "offered_rate": rate,
+           "duration_s": duration, "warmup_s": warmup_s, "slots": slots,
+           "mean_batch": s.get("mean_batch"), "pair_perm_evals_per_s": evals / wall,
+           "matrices_resident": len(mats), "resident_gb": round(resident / 1e9, 1),
+           "config": {"workload": "serving-64", "matrices": 64, "n_range": [500, 30000],
+                      "perms": [999, 9999], "K_range": [2, 12], "factors_per_matrix": [1, 20],
+                      "arrivals": "Poisson"}}
+    del mats
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_bench(args) -> None:
+    """``--serving``: the serving workload alone, one JSON line."""
+    import torch
+    line = serving_run(args.rate, args.duration, args.slots)
+    line.update({"higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+                 "gpu": torch.cuda.get_device_name(0)})
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--serving", action="store_true")
-    ap.add_argument("--rate", type=float, default=20.0)
-    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--rate", type=float, default=60.0)
+    ap.add_argument("--duration", type=float, default=12.0)
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -560,8 +579,17 @@ def main():
                       "copies D's band trapezoids in segments overlapped with the kernels)"}
 
     cpu = None
+    rows_h = lab[:64].cpu().numpy()
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the serving workload on the same GPU, after the step's buffers and the
+        # context's scratch are given back
+        del lab, out
+        Dh = labh = outh = None
+        pm.permanova_release_scratch(ctx.handle)
+        torch.cuda.empty_cache()
+        serving = serving_run(args.rate, args.duration, args.slots)
     if rank == 0 and not args.no_cpu:
-        rows_h = lab[:64].cpu().numpy()
         cpu = oracle_rate(cfg, X, rows_h, 15.0)
 
     if rank == 0:
@@ -581,7 +609,7 @@ def main():
                                   if flush is None else
                                   "L2 flushed between steps (2 x L2 write, untimed)"),
                            "parallelism": f"replicas x{world} (label rows split)"},
-                "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "clocks": clocks,
                 "gpu_launches": int(prof["kernel_launches"]),
                 "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line), flush=True)

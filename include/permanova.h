@@ -149,6 +149,19 @@ int permanova_selftest_wait(permanova_ctx *ctx, uint32_t limit_us, void *stream)
 size_t permanova_scratch_bytes(permanova_ctx *ctx, int form, uint32_t n_dims, uint32_t n_groups,
                                uint64_t n_perms);
 
+/* Bytes of device scratch the context holds now (its arena only grows while
+ * calls need more, up to the budget, and is kept between calls). */
+size_t permanova_scratch_reserved(permanova_ctx *ctx);
+
+/* Grow the context's scratch arena to at least `bytes` now (so later calls
+ * need no allocation of their own).  ENOMEM beyond the budget. */
+int permanova_reserve_scratch(permanova_ctx *ctx, size_t bytes);
+
+/* Wait for the context's device, then free the context's scratch arena (the
+ * next call allocates again).  Lets a server that keeps several contexts
+ * return the memory an idle one holds. */
+int permanova_release_scratch(permanova_ctx *ctx);
+
 /* The paper's permanova_f_stat_sW_T (Sec. 2, Algorithm 1's driver): s_W for
  * n_perms label rows.  Asynchronous on `stream`.
  *   mat              DEVICE, fp32, row-major, n_dims rows of stride ld
@@ -289,8 +302,8 @@ int permanova_test(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64
                    const int32_t *grouping, uint32_t n_groups, uint64_t n_perms, uint64_t seed,
                    permanova_result *out_host, double *out_sW, void *stream);
 
-/* n_tests permutation tests on one matrix in one pass (the batching a server
- * applies to requests on the same matrix with the same n_groups and n_perms).
+/* n_tests permutation tests on one matrix with the same n_groups and n_perms
+ * in one pass (permanova_test_mixed with equal counts).
  *   groupings  DEVICE, n_tests rows of n_dims int32 observed labels (row t =
  *              test t), each in [0, n_groups) with every group non-empty.
  *   seeds      HOST, n_tests permutation seeds.
@@ -304,6 +317,29 @@ int permanova_test(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64
 int permanova_test_batch(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
                          const int32_t *groupings, uint32_t n_tests, uint32_t n_groups,
                          uint64_t n_perms, const uint64_t *seeds, permanova_result *out_host,
+                         double *out_sW, void *stream);
+
+/* Several permutation tests on one matrix with their own group counts and
+ * permutation counts, in as few s_W passes as possible (the fusion a server
+ * applies to the requests waiting on one matrix; Sec. 1 notes that many
+ * tests are typically run on one distance matrix).
+ *   groupings  DEVICE, n_tests rows of n_dims int32 observed labels; row t in
+ *              [0, n_groups[t]) with every group non-empty.
+ *   n_groups   HOST, n_tests group counts (each >= 2 and < n_dims).
+ *   n_perms    HOST, n_tests permutation counts (each >= 1).
+ *   seeds      HOST, n_tests permutation seeds.
+ *   out_host   HOST, n_tests results.
+ *   out_sW     optional DEVICE buffer of sum_t (n_perms[t] + 1) doubles: test
+ *              t's s_W (observed first) after those of tests 0 .. t-1.
+ * Every test runs in the kernel form a lone test of its sizes gets; the tests
+ * of one form share one s_W launch over all their label rows, with the
+ * largest group count among them (each test weighted by its own 1/n_g,
+ * groups it lacks weighted 0).  Each result equals the corresponding
+ * permanova_test call bit for bit.  Synchronises `stream`; errors as
+ * permanova_test (the message names the test). */
+int permanova_test_mixed(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                         const int32_t *groupings, uint32_t n_tests, const uint32_t *n_groups,
+                         const uint64_t *n_perms, const uint64_t *seeds, permanova_result *out_host,
                          double *out_sW, void *stream);
 
 #ifdef __cplusplus

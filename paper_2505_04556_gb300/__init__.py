@@ -93,6 +93,12 @@ def load(path: str | None = None):
         lib.permanova_plan_form.restype = i32
         lib.permanova_scratch_bytes.argtypes = [vp, i32, u32, u32, u64]
         lib.permanova_scratch_bytes.restype = sz
+        lib.permanova_scratch_reserved.argtypes = [vp]
+        lib.permanova_scratch_reserved.restype = sz
+        lib.permanova_reserve_scratch.argtypes = [vp, sz]
+        lib.permanova_reserve_scratch.restype = i32
+        lib.permanova_release_scratch.argtypes = [vp]
+        lib.permanova_release_scratch.restype = i32
         sw_args = [vp, vp, u32, u64, vp, i32, u32, u64, vp, vp, vp]
         lib.permanova_sW.argtypes = sw_args
         lib.permanova_sW.restype = i32
@@ -111,6 +117,9 @@ def load(path: str | None = None):
         lib.permanova_test_batch.argtypes = [vp, vp, u32, u64, vp, u32, u32, u64, vp,
                                              ctypes.POINTER(permanova_result), vp, vp]
         lib.permanova_test_batch.restype = i32
+        lib.permanova_test_mixed.argtypes = [vp, vp, u32, u64, vp, u32, vp, vp, vp,
+                                             ctypes.POINTER(permanova_result), vp, vp]
+        lib.permanova_test_mixed.restype = i32
         lib.permanova_selftest_wait.argtypes = [vp, u32, vp]
         lib.permanova_selftest_wait.restype = i32
         lib.permanova_set_graphs.argtypes = [vp, i32]
@@ -204,6 +213,18 @@ def permanova_scratch_bytes(ctx, form: int, n_dims: int, n_groups: int, n_perms:
     return int(load().permanova_scratch_bytes(ctx, int(form), n_dims, n_groups, n_perms))
 
 
+def permanova_scratch_reserved(ctx) -> int:
+    return int(load().permanova_scratch_reserved(ctx))
+
+
+def permanova_reserve_scratch(ctx, nbytes: int) -> None:
+    _check(ctx, load().permanova_reserve_scratch(ctx, int(nbytes)))
+
+
+def permanova_release_scratch(ctx) -> None:
+    _check(ctx, load().permanova_release_scratch(ctx))
+
+
 def permanova_sW(ctx, mat, n_dims: int, ld: int, groupings, label_type: int, n_groups: int,
                  n_perms: int, inv_group_sizes, out_sW, stream=None) -> None:
     rc = load().permanova_sW(ctx, _ptr(mat), int(n_dims), int(ld), _ptr(groupings), int(label_type),
@@ -236,6 +257,21 @@ def permanova_test_batch(ctx, mat, n_dims: int, ld: int, groupings, n_tests: int
     sd = (ctypes.c_uint64 * n_tests)(*[int(x) & (2**64 - 1) for x in seeds])
     rc = load().permanova_test_batch(ctx, _ptr(mat), int(n_dims), int(ld), _ptr(groupings),
                                      int(n_tests), int(n_groups), int(n_perms),
+                                     ctypes.cast(sd, ctypes.c_void_p), res, _ptr(out_sW),
+                                     _stream(stream))
+    _check(ctx, rc)
+    return [r.as_dict() for r in res]
+
+
+def permanova_test_mixed(ctx, mat, n_dims: int, ld: int, groupings, n_groups, n_perms, seeds,
+                         out_sW=None, stream=None) -> list:
+    T = len(seeds)
+    res = (permanova_result * T)()
+    ks = (ctypes.c_uint32 * T)(*[int(k) for k in n_groups])
+    ps = (ctypes.c_uint64 * T)(*[int(p) for p in n_perms])
+    sd = (ctypes.c_uint64 * T)(*[int(x) & (2**64 - 1) for x in seeds])
+    rc = load().permanova_test_mixed(ctx, _ptr(mat), int(n_dims), int(ld), _ptr(groupings), T,
+                                     ctypes.cast(ks, ctypes.c_void_p), ctypes.cast(ps, ctypes.c_void_p),
                                      ctypes.cast(sd, ctypes.c_void_p), res, _ptr(out_sW),
                                      _stream(stream))
     _check(ctx, rc)

@@ -49,6 +49,30 @@ __host__ __device__ __forceinline__ uint32_t row_for_pair(uint64_t target, uint3
     return lo;
 }
 
+// Weights of the label rows of one s_W launch: one set of K FP64 weights for
+// every row, or one set per test when several tests share the launch (set t
+// covers rows [row_start[t], row_start[t+1]), or rows [t*set_rows,
+// (t+1)*set_rows) when row_start is NULL and set_rows > 0).
+struct WeightMap {
+    const double* w;
+    uint64_t set_rows;          // equal-sized sets (0: see row_start / one set)
+    const uint64_t* row_start;  // DEVICE, n_sets + 1 ascending row offsets, or NULL
+    uint32_t n_sets;
+    uint32_t K;                 // weights per set
+    // The K weights label row p uses.
+    __device__ __forceinline__ const double* row(uint64_t p) const {
+        if (row_start) {
+            uint32_t lo = 0, hi = n_sets - 1;   // last set whose first row is <= p
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) / 2;
+                if (__ldg(row_start + mid) <= p) lo = mid; else hi = mid - 1;
+            }
+            return w + (uint64_t)lo * K;
+        }
+        return set_rows ? w + (p / set_rows) * K : w;
+    }
+};
+
 struct SWProblem {
     const float* mat;
     uint32_t n;
@@ -65,6 +89,13 @@ struct SWProblem {
     // Layout of mat: 0 = row-major with row stride ld; 1 = band trapezoids
     // (see band_trapezoid_offset; tensor-core form only, ld unused).
     uint32_t banded;
+    // Ragged weight sets (override w_set_rows): set t covers label rows
+    // [w_row_start[t], w_row_start[t+1]) (DEVICE, w_sets + 1 entries).
+    const uint64_t* w_row_start;
+    uint32_t w_sets;
+    WeightMap weights() const {
+        return WeightMap{w, w_row_start ? 0ull : w_set_rows, w_row_start, w_sets, K};
+    }
 };
 
 // Band-trapezoid layout of the strict upper triangle (the host entry point's
@@ -89,12 +120,6 @@ __host__ __device__ __forceinline__ const float* d_row(const float* mat, uint64_
     if (!banded) return mat + (uint64_t)i * ld;
     const uint64_t n4 = (n + 3ull) / 4 * 4, I = i >> 7;
     return mat + band_trapezoid_offset(I, n4) + (uint64_t)(i - 128 * I) * (n4 - 128 * I) - 128 * I;
-}
-
-// Weight of group g for label row p.
-__host__ __device__ __forceinline__ const double* weight_row(const double* w, uint64_t p,
-                                                             uint64_t w_set_rows, uint32_t K) {
-    return w_set_rows ? w + (p / w_set_rows) * K : w;
 }
 
 // inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
@@ -178,12 +203,14 @@ struct TestScalars {
     unsigned long long n_ge;
     unsigned long long n_perms;
 };
-// n_tests tests in one pass: sW and out hold n_tests segments / results
-cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
-                                  const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,
-                                  cudaStream_t s);
-cudaError_t launch_permutations_batch(const int32_t* groupings, uint32_t n, uint32_t n_tests,
-                                      uint64_t n_perms, const uint64_t* seeds, void* out,
-                                      int label_type, cudaStream_t s);
+// n_tests tests in one pass: test t owns label rows [rs[t], rs[t+1]) (DEVICE
+// offsets), its observed grouping is row src[t] of `groupings`, its seed
+// seeds[t] and its group count Ks[t]; results go to out[t]
+cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, const uint64_t* rs,
+                                  const uint32_t* Ks, const double* sT_sum, uint32_t n,
+                                  TestScalars* out, cudaStream_t s);
+cudaError_t launch_permutations_batch(const int32_t* groupings, const uint32_t* src, uint32_t n,
+                                      uint32_t n_tests, const uint64_t* rs, uint64_t total_perms,
+                                      const uint64_t* seeds, void* out, int label_type, cudaStream_t s);
 
 }  // namespace pmn

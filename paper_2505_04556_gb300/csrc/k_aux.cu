@@ -251,17 +251,105 @@ cudaError_t launch_permutations(const int32_t* grouping, uint32_t n, uint64_t n_
 }
 
 // ---------------------------------------------------------------------------
+// Several tests in one pass.  Test t owns the label rows [rs[t], rs[t+1]) of
+// the batch (rs: n_tests + 1 ascending offsets in device memory): the first
+// is its observed grouping (row src[t] of `groupings`), the others its
+// n_perms_t = rs[t+1] - rs[t] - 1 permutations, each the same shuffle a
+// single test with that seed draws.
+// ---------------------------------------------------------------------------
+// Last test whose first row is <= row.
+__device__ __forceinline__ uint32_t test_of_row(const uint64_t* __restrict__ rs, uint32_t n_tests,
+                                                uint64_t row) {
+    uint32_t lo = 0, hi = n_tests - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (rs[mid] <= row) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename L>
+__global__ void k_copy_groupings(const int32_t* __restrict__ g, const uint32_t* __restrict__ src,
+                                 uint32_t n, uint32_t n_tests, const uint64_t* __restrict__ rs,
+                                 L* __restrict__ out) {
+    const uint64_t total = (uint64_t)n * rs[n_tests];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+        const uint64_t row = k / n;
+        const uint32_t t = test_of_row(rs, n_tests, row);
+        out[k] = (L)g[(uint64_t)src[t] * n + (k - row * n)];
+    }
+}
+
+// One thread per permutation: permutation index idx runs over all tests'
+// permutations; test t's come after those of tests 0 .. t-1 (rs[t] - t of them).
+template <typename L>
+__global__ void k_fisher_yates_batch(uint32_t n, uint32_t n_tests, const uint64_t* __restrict__ rs,
+                                     const uint64_t* __restrict__ seeds, uint64_t total_perms,
+                                     L* __restrict__ out) {
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total_perms) return;
+    uint32_t lo = 0, hi = n_tests - 1;   // last test with rs[t] - t <= idx
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (rs[mid] - mid <= idx) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t t = lo;
+    const uint32_t p = (uint32_t)(idx - (rs[t] - t) + 1);
+    L* a = out + (rs[t] + p) * n;
+    Philox4x32 rng;
+    const uint64_t seed = seeds[t];
+    rng.k0 = (uint32_t)seed;
+    rng.k1 = (uint32_t)(seed >> 32);
+    rng.c0 = 0u;
+    rng.c2 = p;
+    rng.used = 4;
+    for (uint32_t i = n - 1; i >= 1; --i) {
+        const uint32_t j = rng.bounded(i + 1);
+        const L ai = a[i];
+        a[i] = a[j];
+        a[j] = ai;
+    }
+}
+
+template <typename L>
+static void perms_batch_t(const int32_t* g, const uint32_t* src, uint32_t n, uint32_t n_tests,
+                          const uint64_t* rs, uint64_t total_perms, const uint64_t* seeds, L* out,
+                          cudaStream_t s) {
+    k_copy_groupings<L><<<152 * 8, 256, 0, s>>>(g, src, n, n_tests, rs, out);
+    if (total_perms) {
+        const unsigned blocks = (unsigned)((total_perms + 127) / 128);
+        k_fisher_yates_batch<L><<<blocks, 128, 0, s>>>(n, n_tests, rs, seeds, total_perms, out);
+    }
+}
+
+cudaError_t launch_permutations_batch(const int32_t* groupings, const uint32_t* src, uint32_t n,
+                                      uint32_t n_tests, const uint64_t* rs, uint64_t total_perms,
+                                      const uint64_t* seeds, void* out, int label_type, cudaStream_t s) {
+    if (label_type == LABEL_U8)
+        perms_batch_t<uint8_t>(groupings, src, n, n_tests, rs, total_perms, seeds, (uint8_t*)out, s);
+    else if (label_type == LABEL_U16)
+        perms_batch_t<uint16_t>(groupings, src, n, n_tests, rs, total_perms, seeds, (uint16_t*)out, s);
+    else
+        perms_batch_t<int32_t>(groupings, src, n, n_tests, rs, total_perms, seeds, (int32_t*)out, s);
+    return launched(total_perms ? 2 : 1);
+}
+
+// ---------------------------------------------------------------------------
 // Test statistics: s_T = (sum_{i<j} d^2)/n, F_obs, and the exceedance count
 // #{p >= 1 : s_W[p] <= s_W[0]}.  For fixed s_T, n and K, pseudo-F decreases
 // strictly in s_W, so F_p >= F_obs is the same event as s_W[p] <= s_W_obs.
+// One block per test; test t's label rows are sW[rs[t] .. rs[t+1]), K = Ks[t].
 // ---------------------------------------------------------------------------
-// One block per test; test t's label rows are sW[t*(n_perms+1) ...].
-__global__ void k_finalize(const double* __restrict__ sW_all, uint64_t n_perms,
-                           const double* __restrict__ sT_sum, uint32_t n, uint32_t K,
-                           TestScalars* out_all) {
+__global__ void k_finalize(const double* __restrict__ sW_all, const uint64_t* __restrict__ rs,
+                           const uint32_t* __restrict__ Ks, const double* __restrict__ sT_sum,
+                           uint32_t n, TestScalars* out_all) {
     __shared__ unsigned long long cnt[32];
-    const double* sW = sW_all + (uint64_t)blockIdx.x * (n_perms + 1);
-    TestScalars* out = out_all + blockIdx.x;
+    const uint32_t t = blockIdx.x;
+    const double* sW = sW_all + rs[t];
+    const uint64_t n_perms = rs[t + 1] - rs[t] - 1;
+    const uint32_t K = Ks[t];
+    TestScalars* out = out_all + t;
     const double obs = sW[0];
     unsigned long long c = 0;
     for (uint64_t p = 1 + threadIdx.x; p <= n_perms; p += blockDim.x) c += (sW[p] <= obs) ? 1ull : 0ull;
@@ -282,71 +370,11 @@ __global__ void k_finalize(const double* __restrict__ sW_all, uint64_t n_perms,
     }
 }
 
-cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, uint64_t n_perms,
-                                  const double* sT_sum, uint32_t n, uint32_t K, TestScalars* out,
-                                  cudaStream_t s) {
-    k_finalize<<<n_tests, 1024, 0, s>>>(sW, n_perms, sT_sum, n, K, out);
+cudaError_t launch_finalize_batch(const double* sW, uint32_t n_tests, const uint64_t* rs,
+                                  const uint32_t* Ks, const double* sT_sum, uint32_t n,
+                                  TestScalars* out, cudaStream_t s) {
+    k_finalize<<<n_tests, 1024, 0, s>>>(sW, rs, Ks, sT_sum, n, out);
     return launched(1);
-}
-
-// ---------------------------------------------------------------------------
-// Several tests at once: test t has its own observed grouping (row t of
-// `groupings`) and seed; its label rows are t*(n_perms+1) .. (t+1)*(n_perms+1)-1,
-// the first being the observed grouping.  Each shuffle is the same as a
-// single test's with that seed.
-// ---------------------------------------------------------------------------
-template <typename L>
-__global__ void k_copy_groupings(const int32_t* __restrict__ g, uint32_t n, uint32_t n_tests,
-                                 uint64_t rows_per_test, L* __restrict__ out) {
-    const uint64_t total = (uint64_t)n * rows_per_test * n_tests;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
-        const uint64_t row = k / n, t = row / rows_per_test;
-        out[k] = (L)g[t * n + (k - row * n)];
-    }
-}
-
-template <typename L>
-__global__ void k_fisher_yates_batch(uint32_t n, uint64_t n_perms, uint32_t n_tests,
-                                     const uint64_t* __restrict__ seeds, L* __restrict__ out) {
-    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_perms * n_tests) return;
-    const uint64_t t = idx / n_perms;
-    const uint32_t p = (uint32_t)(idx - t * n_perms + 1);
-    L* a = out + (t * (n_perms + 1) + p) * n;
-    Philox4x32 rng;
-    const uint64_t seed = seeds[t];
-    rng.k0 = (uint32_t)seed;
-    rng.k1 = (uint32_t)(seed >> 32);
-    rng.c0 = 0u;
-    rng.c2 = p;
-    rng.used = 4;
-    for (uint32_t i = n - 1; i >= 1; --i) {
-        const uint32_t j = rng.bounded(i + 1);
-        const L ai = a[i];
-        a[i] = a[j];
-        a[j] = ai;
-    }
-}
-
-template <typename L>
-static void perms_batch_t(const int32_t* g, uint32_t n, uint32_t n_tests, uint64_t n_perms,
-                          const uint64_t* seeds, L* out, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((n_perms * n_tests + 127) / 128);
-    k_copy_groupings<L><<<152 * 8, 256, 0, s>>>(g, n, n_tests, n_perms + 1, out);
-    k_fisher_yates_batch<L><<<blocks, 128, 0, s>>>(n, n_perms, n_tests, seeds, out);
-}
-
-cudaError_t launch_permutations_batch(const int32_t* groupings, uint32_t n, uint32_t n_tests,
-                                      uint64_t n_perms, const uint64_t* seeds, void* out,
-                                      int label_type, cudaStream_t s) {
-    if (label_type == LABEL_U8)
-        perms_batch_t<uint8_t>(groupings, n, n_tests, n_perms, seeds, (uint8_t*)out, s);
-    else if (label_type == LABEL_U16)
-        perms_batch_t<uint16_t>(groupings, n, n_tests, n_perms, seeds, (uint16_t*)out, s);
-    else
-        perms_batch_t<int32_t>(groupings, n, n_tests, n_perms, seeds, (int32_t*)out, s);
-    return launched(2);
 }
 
 }  // namespace pmn

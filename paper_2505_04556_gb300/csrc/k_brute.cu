@@ -30,7 +30,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <typename L, bool VEC>
 __global__ void __launch_bounds__(BR_THREADS)
 k_sw_brute(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __restrict__ labels,
-           uint64_t P, const double* __restrict__ w, uint64_t w_set_rows, uint32_t K, uint32_t n_chunks,
+           uint64_t P, const WeightMap wm, uint32_t K, uint32_t n_chunks,
            double* __restrict__ partials, const DevStatus* __restrict__ st) {
     __shared__ double red[BR_THREADS / 32];
     const uint64_t unit = blockIdx.x;
@@ -47,10 +47,11 @@ k_sw_brute(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __re
     const uint32_t r0 = row_for_pair(total * c / n_chunks, n);
     const uint32_t r1 = row_for_pair(total * (c + 1) / n_chunks, n);
     const L* g = labels + p * n;
+    const double* wrow = wm.row(p);
     double acc = 0.0;
     for (uint32_t i = r0; i < r1 && i + 1 < n; ++i) {
         const uint32_t gi = min(label_at(g, i), K - 1);
-        const double wi = __ldg(weight_row(w, p, w_set_rows, K) + gi);
+        const double wi = __ldg(wrow + gi);
         const float* row = mat + (uint64_t)i * ld;
         float s = 0.f;
         uint32_t j = i + 1;
@@ -112,11 +113,11 @@ static cudaError_t launch_brute_t(const SWProblem& pr, uint32_t n_chunks, double
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     if (vec)
         k_sw_brute<L, true><<<(unsigned)blocks, BR_THREADS, 0, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, pr.P, pr.w, pr.w_set_rows, pr.K, n_chunks,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, pr.P, pr.weights(), pr.K, n_chunks,
             partials, st);
     else
         k_sw_brute<L, false><<<(unsigned)blocks, BR_THREADS, 0, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, pr.P, pr.w, pr.w_set_rows, pr.K, n_chunks,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, pr.P, pr.weights(), pr.K, n_chunks,
             partials, st);
     return launched(1);
 }

@@ -526,8 +526,7 @@ struct GemmArgs {
     const uint32_t* bmax;      // per band: bit pattern of the largest d^2 (sets S_I),
                                // then per band that of the smallest nonzero d^2
     const uint8_t* labels;     // uint8 codes, row stride n_pad, zero padded
-    const double* w;
-    uint64_t w_set_rows;       // label rows per weight set (0: one set)
+    WeightMap wm;              // FP64 weights of each label row
     double* partials;          // n_bands x P
     DevStatus* st;
     uint64_t P;
@@ -897,7 +896,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             for (int grp = 0; grp < g::NMAX / 32; ++grp) {
                 const uint32_t c = 32u * grp + lane;
                 const double wc = (c < used && c / K < nlab)
-                                      ? __ldg(weight_row(a.w, p0 + c / K, a.w_set_rows, K) + c % K) * inv_s : 0.0;
+                                      ? __ldg(a.wm.row(p0 + c / K) + c % K) * inv_s : 0.0;
                 acc64[q4 * g::NMAX + c] = (acc[grp] + (double)colf[grp]) * wc;
             }
             mbar_arrive(epi_bar);
@@ -1070,8 +1069,7 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     a.tiles = (const uint8_t*)scratch;
     a.bmax = reinterpret_cast<const uint32_t*>(a.tiles + tile_bytes_total(gp));
     a.labels = (const uint8_t*)pr.labels;
-    a.w = pr.w;
-    a.w_set_rows = pr.w_set_rows;
+    a.wm = pr.weights();
     a.partials = partials;
     a.st = st;
     a.P = pr.P;

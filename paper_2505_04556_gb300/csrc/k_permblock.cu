@@ -90,8 +90,7 @@ __device__ __forceinline__ void load_col_codes<uint16_t>(const uint16_t* __restr
 template <typename L, bool VEC>
 __global__ void __launch_bounds__(PB_P, 4)
 k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __restrict__ labels,
-               uint64_t lstride, uint64_t P, const double* __restrict__ w_all, uint64_t w_set_rows,
-               uint32_t K,
+               uint64_t lstride, uint64_t P, const WeightMap wm, uint32_t K,
                uint32_t n_pblocks, double* __restrict__ partials, const DevStatus* __restrict__ st) {
     // dynamic shared memory: the D^2 tile, then per (row, thread) the row's
     // FP32 weight and its label (clamped to K - 1)
@@ -111,7 +110,7 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     }
     // inactive threads of the last block mirror the last row so loads stay in bounds
     const L* g = labels + (active ? p : P - 1) * lstride;
-    const double* w = weight_row(w_all, active ? p : P - 1, w_set_rows, K);
+    const double* w = wm.row(active ? p : P - 1);
     const uint32_t r0 = band * PB_T;
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     double total = 0.0;
@@ -202,11 +201,11 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
     if (e != cudaSuccess) return e;
     if (vec)
         k_sw_permblock<L, true><<<(unsigned)blocks, PB_P, smem, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     else
         k_sw_permblock<L, false><<<(unsigned)blocks, PB_P, smem, s>>>(
-            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.w, pr.w_set_rows, pr.K,
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     return launched(1);
 }

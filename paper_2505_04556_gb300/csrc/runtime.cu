@@ -462,6 +462,32 @@ size_t permanova_scratch_bytes(permanova_ctx* ctx, int form, uint32_t n, uint32_
     return L.total;
 }
 
+size_t permanova_scratch_reserved(permanova_ctx* ctx) {
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->arena_size;
+}
+
+int permanova_reserve_scratch(permanova_ctx* ctx, size_t bytes) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    return ensure_arena(ctx, bytes);
+}
+
+int permanova_release_scratch(permanova_ctx* ctx) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graph_cache.clear();
+    if (ctx->arena) CK(cudaFree(ctx->arena), "cudaFree(scratch)");
+    ctx->arena = nullptr;
+    ctx->arena_size = 0;
+    return PERMANOVA_OK;
+}
+
 int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, const void* groupings,
                  int label_type, uint32_t K, uint64_t P, const float* w, double* out, void* stream) {
     if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
@@ -779,20 +805,37 @@ int permanova_permutations(permanova_ctx* ctx, const int32_t* grouping, uint32_t
 int permanova_test(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
                    const int32_t* grouping, uint32_t K, uint64_t P, uint64_t seed,
                    permanova_result* out_host, double* out_sW, void* stream) {
-    return permanova_test_batch(ctx, mat, n, ld, grouping, 1, K, P, &seed, out_host, out_sW, stream);
+    return permanova_test_mixed(ctx, mat, n, ld, grouping, 1, &K, &P, &seed, out_host, out_sW, stream);
 }
 
 int permanova_test_batch(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
                          const int32_t* groupings, uint32_t T, uint32_t K, uint64_t P,
                          const uint64_t* seeds, permanova_result* out_host, double* out_sW,
                          void* stream) {
-    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
-    if (!mat || !groupings || !out_host || !seeds) return fail(PERMANOVA_EINVAL, "NULL pointer argument");
     if (T == 0) return fail(PERMANOVA_EINVAL, "n_tests must be >= 1");
-    if (K < 2) return fail(PERMANOVA_EINVAL, "the test needs n_groups >= 2 (got %u)", K);
-    if (n <= K) return fail(PERMANOVA_EINVAL, "the test needs n_dims > n_groups (pseudo-F undefined)");
+    std::vector<uint32_t> Ks(T, K);
+    std::vector<uint64_t> Ps(T, P);
+    return permanova_test_mixed(ctx, mat, n, ld, groupings, T, Ks.data(), Ps.data(), seeds, out_host,
+                                out_sW, stream);
+}
+
+int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                         const int32_t* groupings, uint32_t T, const uint32_t* Ks, const uint64_t* Ps,
+                         const uint64_t* seeds, permanova_result* out_host, double* out_sW,
+                         void* stream) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    if (!mat || !groupings || !out_host || !seeds || !Ks || !Ps)
+        return fail(PERMANOVA_EINVAL, "NULL pointer argument");
+    if (T == 0) return fail(PERMANOVA_EINVAL, "n_tests must be >= 1");
     if (ld < n) return fail(PERMANOVA_EINVAL, "ld < n_dims");
-    if (P == 0 || P >= 0xFFFFFFFFull) return fail(PERMANOVA_EINVAL, "n_perms out of range");
+    uint32_t Kmax = 0;
+    for (uint32_t t = 0; t < T; ++t) {
+        if (Ks[t] < 2) return fail(PERMANOVA_EINVAL, "test %u: the test needs n_groups >= 2 (got %u)", t, Ks[t]);
+        if (n <= Ks[t])
+            return fail(PERMANOVA_EINVAL, "test %u: the test needs n_dims > n_groups (pseudo-F undefined)", t);
+        if (Ps[t] == 0 || Ps[t] >= 0xFFFFFFFFull) return fail(PERMANOVA_EINVAL, "test %u: n_perms out of range", t);
+        Kmax = std::max(Kmax, Ks[t]);
+    }
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -802,31 +845,68 @@ int permanova_test_batch(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     CK(cudaMemcpyAsync(hg.data(), groupings, hg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
        "copy groupings");
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    std::vector<double> hw((size_t)K * T);
-    std::vector<uint64_t> sizes(K);
+    std::vector<double> hw((size_t)Kmax * T, 0.0);   // test t's weights, groups >= K_t stay 0
+    std::vector<uint64_t> sizes(Kmax);
     for (uint32_t t = 0; t < T; ++t) {
         std::fill(sizes.begin(), sizes.end(), 0);
         for (uint32_t i = 0; i < n; ++i) {
             const int32_t lab = hg[(size_t)t * n + i];
-            if (lab < 0 || (uint32_t)lab >= K)
-                return fail(PERMANOVA_EINVAL, "test %u: grouping[%u] = %d outside [0, %u)", t, i, lab, K);
+            if (lab < 0 || (uint32_t)lab >= Ks[t])
+                return fail(PERMANOVA_EINVAL, "test %u: grouping[%u] = %d outside [0, %u)", t, i, lab, Ks[t]);
             sizes[lab] += 1;
         }
-        for (uint32_t k = 0; k < K; ++k) {
+        for (uint32_t k = 0; k < Ks[t]; ++k) {
             if (sizes[k] == 0) return fail(PERMANOVA_EINVAL, "test %u: group %u is empty", t, k);
-            hw[(size_t)t * K + k] = 1.0 / (double)sizes[k];
+            hw[(size_t)t * Kmax + k] = 1.0 / (double)sizes[k];
         }
     }
 
-    // every test's label rows in one pass; the form is the one a single test
-    // would get, so a batched test gives the same numbers as a lone one
-    const uint64_t per = P + 1, rows = per * T;
-    const int lt = K <= 256 ? LABEL_U8 : K <= 65536 ? LABEL_U16 : LABEL_I32;
-    const int form = plan_form(ctx, n, K, per);
-    SWLayout L;
-    int rc = layout_for(ctx, form, n, ld, nullptr, lt, K, rows, &L);
-    if (rc) return rc;
-    size_t off = L.total;
+    // Each test runs in the kernel form a lone test of its sizes gets; tests of
+    // one form share one s_W pass (label rows of every such test, n_groups =
+    // the largest of them, per-test weights, unused groups weighted 0), so the
+    // batch is processed in form order.  Every per-row result is independent
+    // of the other rows in its launch and of the padded group count, so each
+    // test's s_W, F and p equal those of the same test run alone.
+    std::vector<int> form(T);
+    for (uint32_t t = 0; t < T; ++t) form[t] = plan_form(ctx, n, Ks[t], Ps[t] + 1);
+    std::vector<uint32_t> order(T);
+    for (uint32_t t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return form[x] < form[y]; });
+    std::vector<uint64_t> rs(T + 1, 0);      // row starts in form order
+    std::vector<uint32_t> ks(T);
+    std::vector<uint64_t> sd(T);
+    for (uint32_t k = 0; k < T; ++k) {
+        rs[k + 1] = rs[k] + Ps[order[k]] + 1;
+        ks[k] = Ks[order[k]];
+        sd[k] = seeds[order[k]];
+    }
+    const uint64_t rows = rs[T];
+    const int lt = Kmax <= 256 ? LABEL_U8 : Kmax <= 65536 ? LABEL_U16 : LABEL_I32;
+    // form groups [gb[q], gb[q+1]) of the ordered tests, each with its own
+    // weight table (stride = the group's n_groups) and row starts
+    struct FormGroup { uint32_t t0, t1, K; int form; size_t w_off, rs_off; };
+    std::vector<FormGroup> groups;
+    std::vector<double> gw;
+    std::vector<uint64_t> grs;
+    for (uint32_t k = 0; k < T;) {
+        uint32_t e = k;
+        uint32_t Kg = 0;
+        while (e < T && form[order[e]] == form[order[k]]) Kg = std::max(Kg, ks[e++]);
+        FormGroup fg{k, e, Kg, form[order[k]], gw.size(), grs.size()};
+        for (uint32_t q = k; q < e; ++q)
+            for (uint32_t c = 0; c < Kg; ++c) gw.push_back(hw[(size_t)order[q] * Kmax + c]);
+        for (uint32_t q = k; q <= e; ++q) grs.push_back(rs[q] - rs[k]);
+        groups.push_back(fg);
+        k = e;
+    }
+    size_t sw_scratch = 0;
+    for (const FormGroup& fg : groups) {
+        SWLayout L;
+        int rc = layout_for(ctx, fg.form, n, ld, nullptr, lt, fg.K, rs[fg.t1] - rs[fg.t0], &L);
+        if (rc) return rc;
+        sw_scratch = std::max(sw_scratch, L.total);
+    }
+    size_t off = align_up(sw_scratch);
     const size_t lab_off = off;
     off = align_up(off + (size_t)n * rows * label_bytes(lt));
     const size_t sw_off = off;
@@ -835,46 +915,84 @@ int permanova_test_batch(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     const size_t st_off = off;
     off = align_up(off + (size_t)(chunks + 1) * sizeof(double));
     const size_t w_off = off;
-    off = align_up(off + hw.size() * sizeof(double));
+    off = align_up(off + gw.size() * sizeof(double));
+    const size_t grs_off = off;
+    off = align_up(off + grs.size() * sizeof(uint64_t));
+    const size_t rs_off = off;
+    off = align_up(off + (size_t)(T + 1) * sizeof(uint64_t));
     const size_t seed_off = off;
     off = align_up(off + (size_t)T * sizeof(uint64_t));
+    const size_t ks_off = off;
+    off = align_up(off + (size_t)T * sizeof(uint32_t));
+    const size_t src_off = off;
+    off = align_up(off + (size_t)T * sizeof(uint32_t));
     const size_t res_off = off;
     off = align_up(off + (size_t)T * sizeof(TestScalars));
-    rc = ensure_arena(ctx, off);
+    int rc = ensure_arena(ctx, off);
     if (rc) return rc;
     char* base = static_cast<char*>(ctx->arena);
     void* labels = base + lab_off;
-    double* sW = out_sW ? out_sW : reinterpret_cast<double*>(base + sw_off);
+    double* sW = reinterpret_cast<double*>(base + sw_off);
     double* st_part = reinterpret_cast<double*>(base + st_off);
-    double* wsets = reinterpret_cast<double*>(base + w_off);
+    double* dw = reinterpret_cast<double*>(base + w_off);
+    uint64_t* dgrs = reinterpret_cast<uint64_t*>(base + grs_off);
+    uint64_t* drs = reinterpret_cast<uint64_t*>(base + rs_off);
     uint64_t* dseeds = reinterpret_cast<uint64_t*>(base + seed_off);
+    uint32_t* dks = reinterpret_cast<uint32_t*>(base + ks_off);
+    uint32_t* dsrc = reinterpret_cast<uint32_t*>(base + src_off);
     TestScalars* dres = reinterpret_cast<TestScalars*>(base + res_off);
 
-    CK(cudaMemcpyAsync(dseeds, seeds, (size_t)T * sizeof(uint64_t), cudaMemcpyHostToDevice, s), "copy seeds");
-    CK(cudaMemcpyAsync(wsets, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice, s),
-       "copy weights");
-    CK(launch_permutations_batch(groupings, n, T, P, dseeds, labels, lt, s), "permutation kernels");
-    rc = layout_for(ctx, form, n, ld, labels, lt, K, rows, &L);
-    if (rc) return rc;
-    SWProblem pr{mat, n, ld, labels, lt, K, rows, wsets, sW};
-    pr.w_set_rows = per;
-    rc = run_sW(ctx, L, pr, nullptr, s);
-    if (rc) return rc;
+    CK(cudaMemcpyAsync(dw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, s), "copy weights");
+    CK(cudaMemcpyAsync(dgrs, grs.data(), grs.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s),
+       "copy row starts");
+    CK(cudaMemcpyAsync(drs, rs.data(), rs.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s),
+       "copy row starts");
+    CK(cudaMemcpyAsync(dseeds, sd.data(), sd.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s), "copy seeds");
+    CK(cudaMemcpyAsync(dks, ks.data(), ks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s),
+       "copy group counts");
+    CK(cudaMemcpyAsync(dsrc, order.data(), order.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s),
+       "copy test order");
+    CK(launch_permutations_batch(groupings, dsrc, n, T, drs, rows - T, dseeds, labels, lt, s),
+       "permutation kernels");
+    for (const FormGroup& fg : groups) {
+        const uint64_t r0 = rs[fg.t0], nr = rs[fg.t1] - r0;
+        void* glab = static_cast<char*>(labels) + (size_t)n * r0 * label_bytes(lt);
+        SWLayout L;
+        rc = layout_for(ctx, fg.form, n, ld, glab, lt, fg.K, nr, &L);
+        if (rc) return rc;
+        SWProblem pr{mat, n, ld, glab, lt, fg.K, nr, dw + fg.w_off, sW + r0};
+        pr.w_row_start = dgrs + fg.rs_off;
+        pr.w_sets = fg.t1 - fg.t0;
+        rc = run_sW(ctx, L, pr, nullptr, s);
+        if (rc) return rc;
+    }
     CK(launch_sumsq_triangle(mat, n, ld, chunks, st_part, s), "sum of squares kernel");
     CK(launch_reduce_rows(st_part, chunks, 1, st_part + chunks, s), "reduce s_T");
-    CK(launch_finalize_batch(sW, T, P, st_part + chunks, n, K, dres, s), "finalize kernel");
+    CK(launch_finalize_batch(sW, T, drs, dks, st_part + chunks, n, dres, s), "finalize kernel");
+    if (out_sW) {
+        // caller order: test t's rows after those of tests 0 .. t-1
+        std::vector<uint64_t> dst(T + 1, 0);
+        for (uint32_t t = 0; t < T; ++t) dst[t + 1] = dst[t] + Ps[t] + 1;
+        for (uint32_t k = 0; k < T; ++k) {
+            const uint32_t t = order[k];
+            CK(cudaMemcpyAsync(out_sW + dst[t], sW + rs[k], (size_t)(Ps[t] + 1) * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s),
+               "copy s_W");
+        }
+    }
     std::vector<TestScalars> hres(T);
     CK(cudaMemcpyAsync(hres.data(), dres, (size_t)T * sizeof(TestScalars), cudaMemcpyDeviceToHost, s),
        "copy results");
     rc = read_status(ctx, s);
     if (rc) return rc;
-    for (uint32_t t = 0; t < T; ++t) {
-        out_host[t].s_T = hres[t].s_T;
-        out_host[t].s_W_obs = hres[t].s_W_obs;
-        out_host[t].F_obs = hres[t].F_obs;
-        out_host[t].p_value = hres[t].p_value;
-        out_host[t].n_ge = hres[t].n_ge;
-        out_host[t].n_perms = hres[t].n_perms;
+    for (uint32_t k = 0; k < T; ++k) {
+        const uint32_t t = order[k];
+        out_host[t].s_T = hres[k].s_T;
+        out_host[t].s_W_obs = hres[k].s_W_obs;
+        out_host[t].F_obs = hres[k].F_obs;
+        out_host[t].p_value = hres[k].p_value;
+        out_host[t].n_ge = hres[k].n_ge;
+        out_host[t].n_perms = hres[k].n_perms;
     }
     return PERMANOVA_OK;
 }

@@ -149,3 +149,73 @@ def test_oversized_request_rejected_not_run(matrices):
         assert r.error is not None and "budget" in r.error
     finally:
         srv.close()
+
+
+def test_mixed_batch_equals_single_tests(matrices):
+    """Tests on one matrix with different group counts and permutation counts,
+    run through one permanova_test_mixed call (one s_W pass per kernel form:
+    here the tensor-core form for K <= 32, the perm-block form for K = 40 and
+    the brute force for 9 permutations), equal the same tests run one by one
+    bit for bit, and their s_W rows land in caller order."""
+    import paper_2505_04556_gb300 as pm
+    mats, hosts = matrices
+    n = hosts[1].shape[0]
+    rng = np.random.default_rng(17)
+    Ks = [2, 12, 5, 40, 3, 7]
+    Ps = [199, 99, 499, 149, 9, 299]
+    labs = [synth.observed_labels(synth.largest_remainder_sizes(n, rng.dirichlet(2 * np.ones(K)),
+                                                                min_size=2), 70 + k)
+            for k, K in enumerate(Ks)]
+    seeds = [101 + 5 * k for k in range(len(Ks))]
+    with pm.Context(0) as ctx:
+        single, single_sw = [], []
+        for lab, K, P, sd in zip(labs, Ks, Ps, seeds):
+            o = torch.empty(P + 1, dtype=torch.float64, device="cuda")
+            single.append(ctx.test(mats[1], torch.from_numpy(lab).cuda(), K, P, sd, out_sW=o))
+            single_sw.append(o.cpu().numpy())
+        forms = {pm.permanova_plan_form(ctx.handle, n, K, P + 1) for K, P in zip(Ks, Ps)}
+        assert forms == {pm.FORM_GEMM, pm.FORM_PERMBLOCK, pm.FORM_BRUTE}
+        g = torch.from_numpy(np.stack(labs)).cuda()
+        out = torch.empty(sum(P + 1 for P in Ps), dtype=torch.float64, device="cuda")
+        mixed = pm.permanova_test_mixed(ctx.handle, mats[1], n, n, g, Ks, Ps, seeds, out)
+    off = 0
+    for a, b, sw, P in zip(single, mixed, single_sw, Ps):
+        assert a == b
+        assert np.array_equal(out[off:off + P + 1].cpu().numpy(), sw)
+        off += P + 1
+    ref = oracle.permanova_test(hosts[1], labs[1], Ks[1], Ps[1], seeds[1])
+    np.testing.assert_allclose(single_sw[1], ref["s_W"], rtol=1e-5)
+
+
+def test_server_fuses_different_group_and_permutation_counts(matrices):
+    """Requests on one matrix with different K and P are fused into one call
+    by the server, and each result equals the request served alone."""
+    from paper_2505_04556_gb300.serve import Request, Server
+    mats, hosts = matrices
+    n = hosts[0].shape[0]   # 300 objects: a small matrix, so the padding cap never splits
+
+    def reqs():
+        out = []
+        for k in range(8):
+            K = 2 + (k % 5)
+            sizes = synth.largest_remainder_sizes(n, np.ones(K), min_size=2)
+            out.append(Request(0, synth.observed_labels(sizes, 90 + k), K, (99, 199)[k % 2],
+                               seed=900 + k))
+        return out
+    srv = Server(mats, n_slots=1)
+    try:
+        alone = []
+        for r in reqs():
+            srv.submit(r)
+            assert r.done.wait(120) and r.error is None, r.error
+            alone.append(r.result)
+        mixed = reqs()
+        for r in mixed:
+            srv.submit(r)
+        for r in mixed:
+            assert r.done.wait(120) and r.error is None, r.error
+    finally:
+        srv.close()
+    assert max(r.batch_size for r in mixed) > 1
+    for r, ref in zip(mixed, alone):
+        assert r.result == ref

@@ -283,6 +283,59 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
+def forms_compare(pk: dict, reps: int = 3) -> dict:
+    """Every kernel form on one workload in the same run: euclid-20k (n =
+    20,000, K = 4), 4,000 label rows (512 for the brute force, which re-reads
+    D from HBM per row), the dominant kernel timed with CUDA events inside the
+    library (mean of ``reps`` launches after one warm-up; D is 1.6 GB, larger
+    than L2), each form's roofline fraction, and its largest relative error
+    against the FP64 oracle on 8 rows every form computes."""
+    import torch
+    import oracle
+    import paper_2505_04556_gb300 as pm
+    cfg = synth.recipe("euclid-20k")
+    n, K = cfg["n"], cfg["K"]
+    X = synth.recipe_points(cfg)
+    D = synth.recipe_matrix_device(cfg, X)
+    lab = synth.device_label_rows(cfg["labels"], 4000, cfg["seed_perms"], dtype=torch.uint8)
+    w = torch.from_numpy(cfg["w"]).cuda()
+    idx = np.array([0, 1, 63, 127, 255, 256, 300, 511])
+    ref = oracle.sW_alg1(D.cpu().numpy(), lab[idx].cpu().numpy().astype(np.int32), K,
+                         cfg["w"].astype(np.float64))
+    pairs = n * (n - 1) / 2
+    out = {"workload": "euclid-20k", "n": n, "K": K, "error_rows": idx.tolist()}
+    cases = [("brute", dict(form=pm.FORM_BRUTE), 512),
+             ("permblock_pair", dict(form=pm.FORM_PERMBLOCK, permblock_variant=0), 4000),
+             ("permblock_f32", dict(form=pm.FORM_PERMBLOCK, permblock_variant=1), 4000),
+             ("gemm", dict(form=pm.FORM_GEMM), 4000)]
+    with pm.Context(0) as ctx:
+        for name, plan, rows in cases:
+            pm.permanova_set_plan(ctx.handle, **plan)
+            res = torch.empty(rows, dtype=torch.float64, device="cuda")
+            pm.permanova_sW(ctx.handle, D, n, n, lab[:rows], pm.LABEL_U8, K, rows, w, res)
+            pm.permanova_sync(ctx.handle)
+            pm.permanova_profile_enable(ctx.handle, True)
+            for _ in range(reps):
+                pm.permanova_sW(ctx.handle, D, n, n, lab[:rows], pm.LABEL_U8, K, rows, w, res)
+            prof = pm.permanova_profile_read(ctx.handle)
+            pm.permanova_profile_enable(ctx.handle, False)
+            pm.permanova_sync(ctx.handle)
+            ms = prof["main_kernel_ms"] / max(1, prof["main_kernel_launches"])
+            evals = pairs * rows
+            rl = roofline("gemm" if name == "gemm" else "permblock" if name.startswith("permblock")
+                          else "brute", K, evals, ms, pk, None)
+            got = res.cpu().numpy()[idx]
+            out[name] = {"evals_per_s": evals / (ms / 1e3), "kernel_ms": ms, "rows": rows,
+                         "roofline_frac": rl["frac"], "bound": rl["bound"],
+                         "max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref))}
+        pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
+    out["gemm_over_best_fp32"] = out["gemm"]["evals_per_s"] / max(
+        out["permblock_pair"]["evals_per_s"], out["permblock_f32"]["evals_per_s"])
+    del D, lab
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
                 seed: int = 5005) -> dict:
     """Serving workload: 64 resident matrices (n log-uniform in 500..30,000,
@@ -379,6 +432,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.serving:
         serving_bench(args)
@@ -447,7 +501,10 @@ def main():
 
     # ---- inputs resident in HBM before timing ----
     D = synth.recipe_matrix_device(cfg, X, device=f"cuda:{dev}")
-    n_rows = min(P, (args.warmup + args.steps) * B)
+    # label rows resident for the run: whole batches only, so every step is a
+    # full batch of B rows (the ring of batches wraps when warm-up + steps
+    # batches exceed the workload's permutations)
+    n_rows = max(B, min(P, (args.warmup + args.steps) * B) // B * B)
     lab = synth.device_label_rows(cfg["labels"], n_rows, rank_seed(cfg["seed_perms"], rank),
                                   device=f"cuda:{dev}", dtype=torch.uint8)
     w = torch.from_numpy(cfg["w"]).to(f"cuda:{dev}")
@@ -461,6 +518,12 @@ def main():
                         out[b0:b0 + bb], stream)
         return bb
 
+    # the plan: the autotuner times candidate plans on a sample of the first
+    # batch's label rows (outside the timed region) unless a form is forced
+    if args.form == "auto" and not args.no_autotune:
+        pm.permanova_autotune(ctx.handle, D, n, D.stride(0), lab[:B], pm.LABEL_U8, K, B, w, stream)
+    plan = pm.permanova_plan_describe(ctx.handle, n, K, B)
+    form = plan["form"]
     for k in range(args.warmup):
         step(k)
     pm.permanova_sync(ctx.handle, stream)
@@ -580,7 +643,7 @@ def main():
 
     cpu = None
     rows_h = lab[:64].cpu().numpy()
-    serving = None
+    serving = forms = None
     if rank == 0 and world == 1 and not args.no_serving:
         # the serving workload on the same GPU, after the step's buffers and the
         # context's scratch are given back
@@ -589,6 +652,7 @@ def main():
         pm.permanova_release_scratch(ctx.handle)
         torch.cuda.empty_cache()
         serving = serving_run(args.rate, args.duration, args.slots)
+        forms = forms_compare(peaks())
     if rank == 0 and not args.no_cpu:
         cpu = oracle_rate(cfg, X, rows_h, 15.0)
 
@@ -599,7 +663,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "n": n, "K": K, "P_total": P,
-                           "batch": B, "label_type": "u8", "form": form,
+                           "batch": B, "label_type": "u8", "form": form, "plan": plan,
                            "matrix": {"euclid": f"Gaussian points in R^{cfg['dim']} (group shift "
                                                 f"0.3 sd), Euclidean fp32",
                                       "braycurtis": "Dirichlet(0.5) x 200, Bray-Curtis fp32",
@@ -609,7 +673,8 @@ def main():
                                   if flush is None else
                                   "L2 flushed between steps (2 x L2 write, untimed)"),
                            "parallelism": f"replicas x{world} (label rows split)"},
-                "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "clocks": clocks,
+                "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "forms": forms,
+                "clocks": clocks,
                 "gpu_launches": int(prof["kernel_launches"]),
                 "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line), flush=True)

@@ -113,16 +113,41 @@ const char *permanova_last_error(const permanova_ctx *ctx);
  * planner).  Returns EINVAL for an unknown form. */
 int permanova_set_form(permanova_ctx *ctx, int form);
 
+/* A kernel plan: the form and its knobs (0 = the default of a knob). */
+typedef struct {
+    int form;                     /* permanova_form_t; AUTO restores the planner */
+    int permblock_variant;        /* 0: paired FP16-compare kernel for uint8 codes, 1: FP32 compare-and-set */
+    uint32_t gemm_rows_div;       /* tensor-core form: label rows per tile divided by 1, 2 or 4 */
+    uint32_t gemm_drain_kblocks;  /* tensor-core form: k-blocks between FP64 drains, 1 .. 8 (default 8) */
+    uint32_t brute_chunk_mult;    /* brute force: chunks per label row multiplied by 1 .. 16 */
+} permanova_plan_t;
+
+/* Force a plan (form and knobs) for subsequent calls; NULL or form AUTO
+ * restores the planner.  EINVAL for a knob out of range (a drain interval
+ * above 8 k-blocks is refused: it breaks the 1e-5 accuracy target). */
+int permanova_set_plan(permanova_ctx *ctx, const permanova_plan_t *plan);
+
 /* Form the planner would use (or the forced one) for these sizes. */
 int permanova_plan_form(permanova_ctx *ctx, uint32_t n_dims, uint32_t n_groups, uint64_t n_perms);
 
-/* Autotuner: times every kernel form that can run these sizes on a sample of
- * the given label rows (at most 4,096 rows, about 0.2 s of work), and makes
- * the fastest the planner's choice for calls with the same log2 buckets of
- * n_dims and n_perms and the same n_groups.  Arguments as permanova_sW (no
- * output buffer: the sample's results go to scratch).  *out_form (optional,
- * HOST) receives the chosen permanova_form_t.  Synchronises `stream`; errors
- * as permanova_sW. */
+/* The plan (form and knobs) a permanova_sW call of these sizes would use, as
+ * a one-line JSON object written to `out` (HOST, `cap` bytes), with its
+ * source: "forced", "autotuned" or "rule".  EINVAL if it does not fit. */
+int permanova_plan_describe(permanova_ctx *ctx, uint32_t n_dims, uint32_t n_groups, uint64_t n_perms,
+                            char *out, size_t cap);
+
+/* Autotuner: times candidate plans on a sample of the given label rows (about
+ * 4e12 pair evaluations, 64 to 4,096 rows) and makes the fastest the
+ * planner's choice for calls with the same log2 buckets of n_dims and n_perms
+ * and the same n_groups.  The candidates cover every form that can run these
+ * sizes and each form's knobs: the brute force's chunks per label row (x1,
+ * x2), the perm-block kernel's variant (paired FP16 compares or FP32
+ * compare-and-set), the tensor-core form's label rows per tile (full or
+ * half width) and drain interval (8 or 4 k-blocks: never longer, the accuracy
+ * limit of the 1e-5 target).  Arguments as permanova_sW (no output buffer:
+ * the sample's results go to scratch).  *out_form (optional, HOST) receives
+ * the chosen permanova_form_t.  Synchronises `stream`; errors as
+ * permanova_sW. */
 int permanova_autotune(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
                        const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
                        const float *inv_group_sizes, int *out_form, void *stream);

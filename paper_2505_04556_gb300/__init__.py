@@ -46,6 +46,12 @@ class permanova_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class permanova_plan_t(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("permblock_variant", ctypes.c_int),
+                ("gemm_rows_div", ctypes.c_uint32), ("gemm_drain_kblocks", ctypes.c_uint32),
+                ("brute_chunk_mult", ctypes.c_uint32)]
+
+
 class permanova_profile_t(ctypes.Structure):
     _fields_ = [("main_kernel_ms", ctypes.c_double), ("main_kernel_launches", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("last_form", ctypes.c_int),
@@ -91,6 +97,10 @@ def load(path: str | None = None):
         lib.permanova_set_form.restype = i32
         lib.permanova_plan_form.argtypes = [vp, u32, u32, u64]
         lib.permanova_plan_form.restype = i32
+        lib.permanova_set_plan.argtypes = [vp, ctypes.POINTER(permanova_plan_t)]
+        lib.permanova_set_plan.restype = i32
+        lib.permanova_plan_describe.argtypes = [vp, u32, u32, u64, ctypes.c_char_p, sz]
+        lib.permanova_plan_describe.restype = i32
         lib.permanova_scratch_bytes.argtypes = [vp, i32, u32, u32, u64]
         lib.permanova_scratch_bytes.restype = sz
         lib.permanova_scratch_reserved.argtypes = [vp]
@@ -207,6 +217,20 @@ def permanova_set_form(ctx, form: int) -> None:
 
 def permanova_plan_form(ctx, n_dims: int, n_groups: int, n_perms: int) -> int:
     return int(load().permanova_plan_form(ctx, n_dims, n_groups, n_perms))
+
+
+def permanova_set_plan(ctx, form: int, permblock_variant: int = 0, gemm_rows_div: int = 0,
+                       gemm_drain_kblocks: int = 0, brute_chunk_mult: int = 0) -> None:
+    pl = permanova_plan_t(int(form), int(permblock_variant), int(gemm_rows_div),
+                          int(gemm_drain_kblocks), int(brute_chunk_mult))
+    _check(ctx, load().permanova_set_plan(ctx, ctypes.byref(pl)))
+
+
+def permanova_plan_describe(ctx, n_dims: int, n_groups: int, n_perms: int) -> dict:
+    import json
+    buf = ctypes.create_string_buffer(512)
+    _check(ctx, load().permanova_plan_describe(ctx, int(n_dims), int(n_groups), int(n_perms), buf, 512))
+    return json.loads(buf.value.decode())
 
 
 def permanova_scratch_bytes(ctx, form: int, n_dims: int, n_groups: int, n_perms: int) -> int:

@@ -144,7 +144,8 @@ cudaError_t launch_reduce_rows(const double* partials, uint32_t rows, uint64_t P
                                cudaStream_t s);
 
 // brute force (Algorithm 3 semantics): partials is n_chunks x P
-uint32_t brute_chunks(uint32_t n, int sm_count);
+// mult > 1 splits each label row's triangle into that many times more chunks
+uint32_t brute_chunks(uint32_t n, int sm_count, uint32_t mult = 1);
 cudaError_t launch_brute(const SWProblem& pr, uint32_t n_chunks, double* partials,
                          const DevStatus* st, cudaStream_t s);
 // sum of squares of the strict upper triangle: partials is n_chunks x 1
@@ -154,8 +155,10 @@ cudaError_t launch_sumsq_triangle(const float* mat, uint32_t n, uint64_t ld, uin
 // perm-block CUDA-core form: partials is permblock_bands(n) x P; labels are
 // uint8/uint16 codes with a 16-byte-multiple row stride of lstride elements
 uint32_t permblock_bands(uint32_t n);
+// variant 0: the paired FP16-compare kernel for uint8 codes (default);
+// variant 1: the FP32 compare-and-set kernel
 cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
-                                      const DevStatus* st, cudaStream_t s);
+                                      const DevStatus* st, cudaStream_t s, int variant = 0);
 
 // labels -> uint8/uint16 codes with row stride lstride (padding = 0); labels
 // >= K raise DEV_BAD_LABEL and are clamped to K-1
@@ -172,7 +175,9 @@ struct GemmPlan {
     uint64_t plane_elems;  // bf16 elements per plane (hi or lo) of the banded upper triangle
 };
 bool gemm_available();
-GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P);
+// ppt_div > 1 divides the label rows per tile (narrower MMA tiles, more work
+// units per band)
+GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P, uint32_t ppt_div = 1);
 size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t P);
 // label rows -> (tile, k-block) blocks of uint8 codes read by the GEMM kernel
 size_t gemm_label_bytes(const GemmPlan& gp);
@@ -185,9 +190,10 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
                              uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu);
 // the tensor-core kernel over bands [I0, I1): partials is gp.n_bands x P, this
 // launch writes the rows of its bands
+// drain_kb: k-blocks accumulated in tensor memory between FP64 drains (0 = default)
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu);
+                             uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu, uint32_t drain_kb = 0);
 
 // a bounded wait on an mbarrier that never completes (failure-detection self-test)
 cudaError_t launch_wait_selftest(DevStatus* st, long long limit_cycles, cudaStream_t s);

@@ -95,11 +95,13 @@ k_sw_brute(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* __re
     if (threadIdx.x == 0) partials[(uint64_t)c * P + p] = tot;
 }
 
-uint32_t brute_chunks(uint32_t n, int sm_count) {
+uint32_t brute_chunks(uint32_t n, int sm_count, uint32_t mult) {
     // about 32K pairs per CTA at least, at most 4 CTAs per SM per label row
+    // (times mult)
+    if (mult < 1) mult = 1;
     const uint64_t pairs = pairs_before_row(n, n);
-    uint64_t c = pairs / 32768;
-    const uint64_t cap = (uint64_t)(sm_count > 0 ? sm_count : 152) * 4;
+    uint64_t c = pairs * mult / 32768;
+    const uint64_t cap = (uint64_t)(sm_count > 0 ? sm_count : 152) * 4 * mult;
     if (c > cap) c = cap;
     if (c > n - 1) c = n - 1;
     return c < 1 ? 1u : (uint32_t)c;

@@ -281,12 +281,13 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t c
 // ---------------------------------------------------------------------------
 bool gemm_available() { return true; }
 
-GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P) {
+GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P, uint32_t ppt_div) {
     GemmPlan gp{};
     gp.n_pad = (n + g::BM - 1) / g::BM * g::BM;
     gp.n_bands = gp.n_pad / g::BM;
     uint32_t ppt = K ? g::NMAX / K : 0;
     if (ppt > (uint32_t)g::PPT_MAX) ppt = g::PPT_MAX;
+    if (ppt_div > 1 && ppt >= ppt_div) ppt /= ppt_div;   // narrower tiles: more units per band
     gp.perms_per_tile = ppt;
     gp.n_ptiles = ppt ? (P + ppt - 1) / ppt : 0;
     const uint64_t nb = gp.n_bands;
@@ -1062,7 +1063,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0, uint32_t I1) {
+                             uint32_t I0, uint32_t I1, uint32_t drain_kb) {
     if (I1 > gp.n_bands) I1 = gp.n_bands;
     if (I0 >= I1) return cudaSuccess;
     GemmArgs a;
@@ -1082,8 +1083,9 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
     a.I0 = I0;
     a.I1 = I1;
-    // accumulation length in TMEM between FP64 drains (tuning/testing override)
-    a.drain_kb = g::DRAIN_KB;
+    // accumulation length in TMEM between FP64 drains: the plan's, else the
+    // default (the environment variable overrides both; accuracy studies only)
+    a.drain_kb = drain_kb ? drain_kb : (uint32_t)g::DRAIN_KB;
     if (const char* env = getenv("PERMANOVA_GEMM_DRAIN")) {
         const int v = atoi(env);
         if (v >= 1 && v <= 4096) a.drain_kb = (uint32_t)v;

@@ -183,6 +183,150 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
     if (active) partials[(uint64_t)band * P + p] = total;
 }
 
+// ---------------------------------------------------------------------------
+// Paired variant (uint8 codes): each thread evaluates TWO label rows p and p'
+// (p' = p + 128) at once.  Its 64 column labels of both rows are held as FP16
+// pairs (0x43Lp, 0x43Lp': distinct finite values for the 256 byte values), and
+// one packed FP16 equality test against the row key (0x43g_p(i), 0x43g_p'(i))
+// sets two predicates, which gate two FP32 adds of the same d^2:
+//   setp.eq.f16x2  P|Q, cl[j], key     (one compare for two evaluations)
+//   @P add.f32     acc_p,  acc_p,  d2
+//   @Q add.f32     acc_p', acc_p', d2
+// so a pair-evaluation costs one compare and two adds, none of them a
+// compare-and-set.  Row segments are summed in FP32 (two chains per label
+// row), weighted once per row segment (Algorithm 2) in FP32 into an 8-row
+// group sum, and group sums are added in FP64, as in the kernel above.  The
+// weights are read per row from the (L1-resident) weight table.
+// ---------------------------------------------------------------------------
+constexpr int PB2_THREADS = 128;              // threads per CTA
+constexpr int PB2_ROWS = 2 * PB2_THREADS;     // label rows per CTA
+constexpr uint32_t PB2_LAB_BYTES = PB_T * PB2_THREADS * 2;   // row labels of p and p': 16 KB
+constexpr uint32_t pb2_smem_bytes() { return PB_D2_BYTES + PB2_LAB_BYTES; }
+
+// acc0 += d where the low FP16 halves of a and b are equal, acc1 += d where
+// the high halves are.
+__device__ __forceinline__ void pair_add(float& acc0, float& acc1, uint32_t a, uint32_t b, float d) {
+    asm("{\n\t.reg .pred p, q;\n\tsetp.eq.f16x2 p|q, %2, %3;\n\t"
+        "@p add.f32 %0, %0, %4;\n\t@q add.f32 %1, %1, %4;\n\t}"
+        : "+f"(acc0), "+f"(acc1)
+        : "r"(a), "r"(b), "f"(d));
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(PB2_THREADS, 4)
+k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
+                    const uint8_t* __restrict__ labels, uint64_t lstride, uint64_t P, const WeightMap wm,
+                    uint32_t K, uint32_t n_pblocks, double* __restrict__ partials,
+                    const DevStatus* __restrict__ st) {
+    extern __shared__ __align__(16) uint8_t pb_smem[];
+    float (*d2)[PB_T] = reinterpret_cast<float (*)[PB_T]>(pb_smem);
+    uint16_t (*lrow)[PB2_THREADS] = reinterpret_cast<uint16_t (*)[PB2_THREADS]>(pb_smem + PB_D2_BYTES);
+    const uint32_t band = blockIdx.x / n_pblocks;
+    const uint32_t q = blockIdx.x % n_pblocks;
+    const uint64_t pa = (uint64_t)q * PB2_ROWS + threadIdx.x, pb = pa + PB2_THREADS;
+    const bool act_a = pa < P, act_b = pb < P;
+    if (__syncthreads_or(st->code != DEV_OK)) {
+        if (act_a) partials[(uint64_t)band * P + pa] = 0.0;
+        if (act_b) partials[(uint64_t)band * P + pb] = 0.0;
+        return;
+    }
+    // inactive label rows mirror the last row so every load stays in bounds
+    const uint64_t ra = act_a ? pa : P - 1, rb = act_b ? pb : P - 1;
+    const uint8_t* ga = labels + ra * lstride;
+    const uint8_t* gb = labels + rb * lstride;
+    const double* wa = wm.row(ra);
+    const double* wb = wm.row(rb);
+    const uint32_t r0 = band * PB_T;
+    const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
+    for (uint32_t r = 0; r < rows; ++r) {
+        const uint32_t la = min((uint32_t)ga[r0 + r], K - 1), lb = min((uint32_t)gb[r0 + r], K - 1);
+        lrow[r][threadIdx.x] = (uint16_t)(la | (lb << 8));
+    }
+    double tot_a = 0.0, tot_b = 0.0;
+
+    for (uint32_t j0 = r0; j0 < n; j0 += PB_T) {
+        __syncthreads();  // the previous tile has been consumed
+#pragma unroll
+        for (int e = threadIdx.x; e < PB_T * PB_T / 4; e += PB2_THREADS) {
+            const int rr = e >> 4, cc = (e & 15) * 4;
+            const uint32_t i = r0 + rr, j = j0 + cc;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) {
+                const float* src = mat + (uint64_t)i * ld + j;
+                if (VEC && j + 3 < n) {
+                    v = __ldg(reinterpret_cast<const float4*>(src));
+                } else {
+                    if (j < n) v.x = __ldg(src);
+                    if (j + 1 < n) v.y = __ldg(src + 1);
+                    if (j + 2 < n) v.z = __ldg(src + 2);
+                    if (j + 3 < n) v.w = __ldg(src + 3);
+                }
+            }
+            v.x = (j > i && j < n) ? v.x * v.x : 0.f;
+            v.y = (j + 1 > i && j + 1 < n) ? v.y * v.y : 0.f;
+            v.z = (j + 2 > i && j + 2 < n) ? v.z * v.z : 0.f;
+            v.w = (j + 3 > i && j + 3 < n) ? v.w * v.w : 0.f;
+            *reinterpret_cast<float4*>(&d2[rr][cc]) = v;
+        }
+        // column labels of both rows as FP16 pairs (padding beyond n is label 0;
+        // its d^2 is 0)
+        uint32_t cl[PB_T];
+        if (j0 + PB_T <= n) {
+            const uint4* sa = reinterpret_cast<const uint4*>(ga + j0);
+            const uint4* sb = reinterpret_cast<const uint4*>(gb + j0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const uint4 va = __ldg(sa + h), vb = __ldg(sb + h);
+                const uint32_t xa[4] = {va.x, va.y, va.z, va.w}, xb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t lo = __byte_perm(xa[t], xb[t], 0x5140);   // a0 b0 a1 b1
+                    const uint32_t hi = __byte_perm(xa[t], xb[t], 0x7362);   // a2 b2 a3 b3
+                    cl[16 * h + 4 * t + 0] = __byte_perm(lo, 0x43u, 0x4140);
+                    cl[16 * h + 4 * t + 1] = __byte_perm(lo, 0x43u, 0x4342);
+                    cl[16 * h + 4 * t + 2] = __byte_perm(hi, 0x43u, 0x4140);
+                    cl[16 * h + 4 * t + 3] = __byte_perm(hi, 0x43u, 0x4342);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < PB_T; ++c) {
+                const uint32_t j = j0 + c;
+                const uint32_t a = j < n ? ga[j] : 0u, b = j < n ? gb[j] : 0u;
+                cl[c] = 0x43004300u | a | (b << 16);
+            }
+        }
+        __syncthreads();
+
+        for (uint32_t rg = 0; rg < rows; rg += PB_G) {
+            const uint32_t rend = min(rg + PB_G, rows);
+            float grp_a = 0.f, grp_b = 0.f;
+#pragma unroll 2
+            for (uint32_t r = rg; r < rend; ++r) {
+                const uint32_t lab = lrow[r][threadIdx.x];
+                const uint32_t key = __byte_perm(lab, 0x43u, 0x4140);     // (0x43 la, 0x43 lb)
+                const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
+                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+                for (int c4 = 0; c4 < PB_T / 4; ++c4) {
+                    const float4 dv = drow[c4];
+                    pair_add(a0, b0, cl[4 * c4 + 0], key, dv.x);
+                    pair_add(a1, b1, cl[4 * c4 + 1], key, dv.y);
+                    pair_add(a0, b0, cl[4 * c4 + 2], key, dv.z);
+                    pair_add(a1, b1, cl[4 * c4 + 3], key, dv.w);
+                }
+                // each row segment weighted once (Algorithm 2)
+                grp_a = fmaf(a0 + a1, (float)__ldg(wa + (lab & 0xFFu)), grp_a);
+                grp_b = fmaf(b0 + b1, (float)__ldg(wb + (lab >> 8)), grp_b);
+            }
+            tot_a += (double)grp_a;
+            tot_b += (double)grp_b;
+        }
+    }
+    if (act_a) partials[(uint64_t)band * P + pa] = tot_a;
+    if (act_b) partials[(uint64_t)band * P + pb] = tot_b;
+}
+
 uint32_t permblock_bands(uint32_t n) { return (n - 1 + PB_T - 1) / PB_T; }
 
 template <typename L>
@@ -210,12 +354,40 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
     return launched(1);
 }
 
+static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double* partials,
+                                  const DevStatus* st, cudaStream_t s) {
+    const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
+    const uint32_t n_bands = permblock_bands(pr.n);
+    const uint64_t n_pblocks = (pr.P + PB2_ROWS - 1) / PB2_ROWS;
+    const uint64_t blocks = (uint64_t)n_bands * n_pblocks;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    const uint32_t smem = pb2_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sw_permblock_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (vec)
+        k_sw_permblock_pair<true><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+            pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
+            (uint32_t)n_pblocks, partials, st);
+    else
+        k_sw_permblock_pair<false><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+            pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
+            (uint32_t)n_pblocks, partials, st);
+    return launched(1);
+}
+
 // pr.labels must be uint8 (pr.label_type == LABEL_U8) or uint16 codes with a
 // row stride of lstride elements, lstride * sizeof(code) a multiple of 16 and
-// the base address 16-byte aligned.
+// the base address 16-byte aligned.  variant 0: the paired FP16-compare
+// kernel for uint8 codes (the FP32 compare-and-set kernel for uint16);
+// variant 1: the FP32 compare-and-set kernel for both.
 cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
-                                      const DevStatus* st, cudaStream_t s) {
-    if (pr.label_type == LABEL_U8) return launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
+                                      const DevStatus* st, cudaStream_t s, int variant) {
+    if (pr.label_type == LABEL_U8)
+        return variant == 0 ? launch_pb_pair(pr, lstride, partials, st, s)
+                            : launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
     return launch_pb_t<uint16_t>(pr, lstride, partials, st, s);
 }
 

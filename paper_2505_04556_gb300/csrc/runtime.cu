@@ -18,7 +18,7 @@
 using namespace pmn;
 
 namespace {
-// (log2 bucket of n, n_groups, log2 bucket of n_perms) -> tuned form
+// (log2 bucket of n, n_groups, log2 bucket of n_perms) -> tuned plan
 using TuneKey = std::tuple<int, uint32_t, int>;
 // every argument of a permanova_sW call plus the form and the scratch arena
 using GraphKey = std::tuple<const void*, uint32_t, uint64_t, const void*, int, uint32_t, uint64_t,
@@ -30,12 +30,27 @@ int log2_bucket(uint64_t x) {
 }
 }  // namespace
 
+// A kernel plan: the form and the knobs of that form.
+struct Plan {
+    int form = PERMANOVA_FORM_BRUTE;
+    int pb_variant = 0;          // perm-block: 0 paired FP16 compares (uint8 codes), 1 FP32 compare-and-set
+    uint32_t gemm_ppt_div = 1;   // tensor-core form: label rows per tile divided by this
+    uint32_t gemm_drain = 0;     // tensor-core form: k-blocks between FP64 drains (0 = default, 8)
+    uint32_t brute_mult = 1;     // brute force: chunks per label row multiplied by this
+    bool tuned = false;
+    bool operator==(const Plan& o) const {
+        return form == o.form && pb_variant == o.pb_variant && gemm_ppt_div == o.gemm_ppt_div &&
+               gemm_drain == o.gemm_drain && brute_mult == o.brute_mult;
+    }
+};
+
 struct permanova_ctx {
     int device = 0;
     int sm_count = 0;
     size_t budget = 0;
     int forced_form = PERMANOVA_FORM_AUTO;
-    std::map<TuneKey, int> tuned;               // autotuner results
+    Plan forced_plan;                           // knobs of a forced plan (permanova_set_plan)
+    std::map<TuneKey, Plan> tuned;              // autotuner results
     bool graphs = false;                        // replay captured launch sequences
     struct CachedGraph {
         cudaGraphExec_t exec;
@@ -109,6 +124,7 @@ size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 // Scratch carve-up for one s_W call.
 struct SWLayout {
     int form = 0;
+    Plan plan;
     uint32_t part_rows = 0;     // rows of the FP64 partials table
     size_t part_off = 0;
     bool repack = false;        // labels re-laid out as codes
@@ -122,26 +138,41 @@ struct SWLayout {
 
 int label_bytes(int t) { return t == LABEL_U8 ? 1 : t == LABEL_U16 ? 2 : 4; }
 
-int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
-    if (ctx->forced_form != PERMANOVA_FORM_AUTO) return ctx->forced_form;
+Plan plan_for(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
+    Plan pl;
+    if (ctx->forced_form != PERMANOVA_FORM_AUTO) return ctx->forced_plan;
     auto it = ctx->tuned.find(TuneKey{log2_bucket(n), K, log2_bucket(P)});
     if (it != ctx->tuned.end()) return it->second;
     // The tensor-core form costs 4K flops per pair and label row (two 16-bit
     // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
     // Measured on a GB300 at n = 20,000 with 4,000 label rows: the GEMM form is
     // 2.22x the perm-block form at K = 16, 1.11x at K = 32 and 0.85x at K = 40.
-    if (gemm_available() && K <= 32 && n >= 256 && P >= 32) return PERMANOVA_FORM_GEMM;
-    if (P >= 16 && K <= 65536) return PERMANOVA_FORM_PERMBLOCK;
-    return PERMANOVA_FORM_BRUTE;
+    if (gemm_available() && K <= 32 && n >= 256 && P >= 32) pl.form = PERMANOVA_FORM_GEMM;
+    else if (P >= 16 && K <= 65536) pl.form = PERMANOVA_FORM_PERMBLOCK;
+    else pl.form = PERMANOVA_FORM_BRUTE;
+    return pl;
 }
 
-int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, const void* labels,
+Plan plan_of_form(int form) {
+    Plan pl;
+    pl.form = form;
+    return pl;
+}
+
+int plan_form(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
+    return plan_for(ctx, n, K, P).form;
+}
+
+int layout_for(const permanova_ctx* ctx, const Plan& plan_in, uint32_t n, uint64_t ld, const void* labels,
                int label_type, uint32_t K, uint64_t P, SWLayout* L) {
+    const Plan plan = plan_in;   // a copy: plan_in may be L->plan, reset on the next line
     *L = SWLayout{};
+    const int form = plan.form;
     L->form = form;
+    L->plan = plan;
     size_t off = 0;
     if (form == PERMANOVA_FORM_BRUTE) {
-        L->part_rows = brute_chunks(n, ctx->sm_count);
+        L->part_rows = brute_chunks(n, ctx->sm_count, plan.brute_mult);
     } else if (form == PERMANOVA_FORM_PERMBLOCK) {
         if (K > 65536)
             return fail(PERMANOVA_EUNSUPPORTED, "perm-block form needs n_groups <= 65536 (got %u)", K);
@@ -156,7 +187,7 @@ int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, cons
         if (!gemm_available()) return fail(PERMANOVA_EUNSUPPORTED, "GEMM form not built");
         if (K > 256) return fail(PERMANOVA_EUNSUPPORTED, "GEMM form needs n_groups <= 256 (got %u)", K);
         if (n < 2) return fail(PERMANOVA_EINVAL, "n_dims < 2");
-        const GemmPlan gp = gemm_plan(n, K, P);
+        const GemmPlan gp = gemm_plan(n, K, P, plan.gemm_ppt_div);
         L->part_rows = gp.n_bands;
         L->code_type = LABEL_U8;
         L->repack = true;  // the GEMM form reads 16-byte aligned, zero-padded uint8 rows
@@ -170,12 +201,12 @@ int layout_for(const permanova_ctx* ctx, int form, uint32_t n, uint64_t ld, cons
     if (L->repack) {
         L->lab_off = off;
         const size_t lab = form == PERMANOVA_FORM_GEMM
-                               ? gemm_label_bytes(gemm_plan(n, K, P))
+                               ? gemm_label_bytes(gemm_plan(n, K, P, plan.gemm_ppt_div))
                                : (size_t)L->lstride * P * label_bytes(L->code_type);
         off = align_up(off + lab);
     }
     if (form == PERMANOVA_FORM_GEMM) {
-        const GemmPlan gp = gemm_plan(n, K, P);
+        const GemmPlan gp = gemm_plan(n, K, P, plan.gemm_ppt_div);
         L->gemm_off = off;
         off = align_up(off + gemm_scratch_bytes(gp, P));
     }
@@ -309,7 +340,8 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
         if (L.repack) {
             void* codes = base + L.lab_off;
             if (L.form == PERMANOVA_FORM_GEMM)
-                CK(launch_repack_gemm(pr.labels, pr.label_type, pr.n, pr.P, pr.K, gemm_plan(pr.n, pr.K, pr.P),
+                CK(launch_repack_gemm(pr.labels, pr.label_type, pr.n, pr.P, pr.K,
+                                      gemm_plan(pr.n, pr.K, pr.P, L.plan.gemm_ppt_div),
                                       codes, ctx->status, s),
                    "repack labels");
             else
@@ -327,17 +359,20 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
             CK(wait_all_rows(), "wait for the matrix");
             int rc = profile_begin(ctx, s);
             if (rc) return rc;
-            CK(launch_permblock_internal(q, L.lstride, partials, ctx->status, s), "perm-block kernel");
+            CK(launch_permblock_internal(q, L.lstride, partials, ctx->status, s, L.plan.pb_variant),
+               "perm-block kernel");
             rc = profile_end(ctx, s);
             if (rc) return rc;
         } else {
-            const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P);
+            const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P, L.plan.gemm_ppt_div);
             void* gs = base + L.gemm_off;
             if (!arr) {
                 CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
                 int rc = profile_begin(ctx, s);
                 if (rc) return rc;
-                CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s), "GEMM kernel");
+                CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s, 0, 0xFFFFFFFFu,
+                                    L.plan.gemm_drain),
+                   "GEMM kernel");
                 rc = profile_end(ctx, s);
                 if (rc) return rc;
             } else {
@@ -353,7 +388,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                     CK(launch_gemm_prep(q, gp, gs, sk, arr->band[k], arr->band[k + 1]),
                        "GEMM operand preparation");
                     CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, sk, arr->band[k],
-                                        arr->band[k + 1]),
+                                        arr->band[k + 1], L.plan.gemm_drain),
                        "GEMM kernel");
                 }
                 CK(cudaEventRecord(arr->join, arr->s2), "join segment streams");
@@ -443,6 +478,35 @@ int permanova_set_form(permanova_ctx* ctx, int form) {
         return fail(PERMANOVA_EINVAL, "unknown form %d", form);
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->forced_form = form;
+    ctx->forced_plan = plan_of_form(form);
+    return PERMANOVA_OK;
+}
+
+int permanova_set_plan(permanova_ctx* ctx, const permanova_plan_t* plan) {
+    if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!plan || plan->form == PERMANOVA_FORM_AUTO) {
+        ctx->forced_form = PERMANOVA_FORM_AUTO;
+        ctx->forced_plan = Plan{};
+        return PERMANOVA_OK;
+    }
+    if (plan->form < PERMANOVA_FORM_BRUTE || plan->form > PERMANOVA_FORM_GEMM)
+        return fail(PERMANOVA_EINVAL, "unknown form %d", plan->form);
+    if (plan->permblock_variant < 0 || plan->permblock_variant > 1)
+        return fail(PERMANOVA_EINVAL, "perm-block variant must be 0 or 1");
+    if (plan->gemm_rows_div != 0 && plan->gemm_rows_div != 1 && plan->gemm_rows_div != 2 &&
+        plan->gemm_rows_div != 4)
+        return fail(PERMANOVA_EINVAL, "gemm_rows_div must be 1, 2 or 4");
+    if (plan->gemm_drain_kblocks > 8)
+        return fail(PERMANOVA_EINVAL, "gemm_drain_kblocks above 8 breaks the 1e-5 accuracy target");
+    if (plan->brute_chunk_mult > 16) return fail(PERMANOVA_EINVAL, "brute_chunk_mult must be <= 16");
+    Plan pl = plan_of_form(plan->form);
+    pl.pb_variant = plan->permblock_variant;
+    pl.gemm_ppt_div = plan->gemm_rows_div ? plan->gemm_rows_div : 1;
+    pl.gemm_drain = plan->gemm_drain_kblocks;
+    pl.brute_mult = plan->brute_chunk_mult ? plan->brute_chunk_mult : 1;
+    ctx->forced_form = plan->form;
+    ctx->forced_plan = pl;
     return PERMANOVA_OK;
 }
 
@@ -455,10 +519,10 @@ int permanova_plan_form(permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) 
 size_t permanova_scratch_bytes(permanova_ctx* ctx, int form, uint32_t n, uint32_t K, uint64_t P) {
     if (!ctx || n < 2 || K == 0 || P == 0) return 0;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (form == PERMANOVA_FORM_AUTO) form = plan_form(ctx, n, K, P);
+    const Plan pl = form == PERMANOVA_FORM_AUTO ? plan_for(ctx, n, K, P) : plan_of_form(form);
     SWLayout L;
     // worst case: labels need a repack
-    if (layout_for(ctx, form, n, n, nullptr, LABEL_I32, K, P, &L) != PERMANOVA_OK) return 0;
+    if (layout_for(ctx, pl, n, n, nullptr, LABEL_I32, K, P, &L) != PERMANOVA_OK) return 0;
     return L.total;
 }
 
@@ -497,7 +561,7 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SWLayout L;
-    rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, groupings, label_type, K, P, &L);
+    rc = layout_for(ctx, plan_for(ctx, n, K, P), n, ld, groupings, label_type, K, P, &L);
     if (rc) return rc;
     rc = ensure_arena(ctx, L.total);
     if (rc) return rc;
@@ -508,7 +572,9 @@ int permanova_sW(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, 
                            cap == cudaStreamCaptureStatusNone;
     if (!use_graph) return run_sW(ctx, L, pr, w, s);
     // replay the launch sequence of an identical earlier call, or capture it now
-    const GraphKey key{mat, n, ld, groupings, label_type, K, P, w, out, ctx->arena, L.form, nullptr};
+    const int plan_code = L.form + 8 * (L.plan.pb_variant + 2 * ((int)L.plan.gemm_ppt_div +
+                                                          16 * ((int)L.plan.gemm_drain + 64 * (int)L.plan.brute_mult)));
+    const GraphKey key{mat, n, ld, groupings, label_type, K, P, w, out, ctx->arena, plan_code, nullptr};
     auto it = ctx->graph_cache.find(key);
     bool fresh = false;
     if (it == ctx->graph_cache.end()) {
@@ -571,24 +637,46 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // a sample of the caller's label rows sized to ~0.2 s of the fastest form
+    // a sample of the caller's label rows sized to ~4e12 pair evaluations
+    // (about 0.1 s of the tensor-core form), at least 64 rows, at most 4,096
     const double pairs = (double)n * (n - 1) / 2.0;
-    uint64_t Ps = (uint64_t)std::max(64.0, 4e11 / std::max(pairs, 1.0));
+    uint64_t Ps = (uint64_t)std::max(64.0, 4e12 / std::max(pairs, 1.0));
     Ps = std::min<uint64_t>(Ps, std::min<uint64_t>(P, 4096));
-    const int forms[3] = {PERMANOVA_FORM_BRUTE, PERMANOVA_FORM_PERMBLOCK, PERMANOVA_FORM_GEMM};
+    // candidate plans: every form with its knobs.  The drain interval of the
+    // tensor-core form stays at 8 k-blocks or fewer, the accuracy limit of the
+    // 1e-5 target (the worst case measured at 8 is 5.2e-6).
+    std::vector<Plan> cands;
+    for (uint32_t mult : {1u, 2u}) {
+        Plan pl = plan_of_form(PERMANOVA_FORM_BRUTE);
+        pl.brute_mult = mult;
+        cands.push_back(pl);
+    }
+    for (int var : {0, 1}) {
+        if (var == 0 && K > 256) continue;
+        Plan pl = plan_of_form(PERMANOVA_FORM_PERMBLOCK);
+        pl.pb_variant = var;
+        cands.push_back(pl);
+    }
+    for (uint32_t div : {1u, 2u})
+        for (uint32_t drain : {8u, 4u}) {
+            Plan pl = plan_of_form(PERMANOVA_FORM_GEMM);
+            pl.gemm_ppt_div = div;
+            pl.gemm_drain = drain;
+            cands.push_back(pl);
+        }
     double best_t = 1e300;
-    int best = PERMANOVA_FORM_BRUTE;
+    Plan best = plan_of_form(PERMANOVA_FORM_BRUTE);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
     if (cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
         cudaEventDestroy(e0);
         return cuda_fail(e, "cudaEventCreate");
     }
-    for (int form : forms) {
+    for (const Plan& pl : cands) {
         // the brute force re-reads D per label row: skip it where it cannot win
-        if (form == PERMANOVA_FORM_BRUTE && Ps > 64 && pairs * Ps > 4e11) continue;
+        if (pl.form == PERMANOVA_FORM_BRUTE && Ps > 64 && pairs * Ps > 4e11) continue;
         SWLayout L;
-        if (layout_for(ctx, form, n, ld, groupings, label_type, K, Ps, &L) != PERMANOVA_OK) continue;
+        if (layout_for(ctx, pl, n, ld, groupings, label_type, K, Ps, &L) != PERMANOVA_OK) continue;
         const size_t out_off = align_up(L.total);
         if (ensure_arena(ctx, out_off + (size_t)Ps * sizeof(double)) != PERMANOVA_OK) continue;
         double* out = reinterpret_cast<double*>(static_cast<char*>(ctx->arena) + out_off);
@@ -601,7 +689,7 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
              cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
         if (ok && ms < best_t) {
             best_t = ms;
-            best = form;
+            best = pl;
         }
     }
     cudaEventDestroy(e0);
@@ -609,8 +697,37 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
     cudaGetLastError();
     rc = read_status(ctx, s);
     if (rc) return rc;
+    best.tuned = true;
     ctx->tuned[TuneKey{log2_bucket(n), K, log2_bucket(P)}] = best;
-    if (out_form) *out_form = best;
+    if (out_form) *out_form = best.form;
+    return PERMANOVA_OK;
+}
+
+int permanova_plan_describe(permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P, char* out, size_t cap) {
+    if (!ctx || !out || cap == 0) return fail(PERMANOVA_EINVAL, "NULL argument");
+    if (n < 2 || K == 0 || P == 0) return fail(PERMANOVA_EINVAL, "invalid sizes");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const Plan pl = plan_for(ctx, n, K, P);
+    const char* src = ctx->forced_form != PERMANOVA_FORM_AUTO ? "forced" : pl.tuned ? "autotuned" : "rule";
+    int m = 0;
+    if (pl.form == PERMANOVA_FORM_GEMM) {
+        const GemmPlan gp = gemm_plan(n, K, P, pl.gemm_ppt_div);
+        m = snprintf(out, cap,
+                     "{\"form\": \"gemm\", \"source\": \"%s\", \"label_rows_per_tile\": %u, "
+                     "\"mma_n\": %u, \"drain_kblocks\": %u, \"band_rows\": 128, \"kblock_cols\": 64}",
+                     src, gp.perms_per_tile, (gp.perms_per_tile * K + 15) / 16 * 16,
+                     pl.gemm_drain ? pl.gemm_drain : 8u);
+    } else if (pl.form == PERMANOVA_FORM_PERMBLOCK) {
+        const bool pair = pl.pb_variant == 0 && K <= 256;
+        m = snprintf(out, cap,
+                     "{\"form\": \"permblock\", \"source\": \"%s\", \"variant\": \"%s\", "
+                     "\"label_rows_per_block\": %u, \"tile\": 64}",
+                     src, pair ? "paired f16x2 compare" : "f32 compare-and-set", pair ? 256u : 128u);
+    } else {
+        m = snprintf(out, cap, "{\"form\": \"brute\", \"source\": \"%s\", \"chunks_per_row\": %u}", src,
+                     brute_chunks(n, ctx->sm_count, pl.brute_mult));
+    }
+    if (m < 0 || (size_t)m >= cap) return fail(PERMANOVA_EINVAL, "buffer too small");
     return PERMANOVA_OK;
 }
 
@@ -672,7 +789,7 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SWLayout L;
-    rc = layout_for(ctx, plan_form(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
+    rc = layout_for(ctx, plan_for(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
     if (rc) return rc;
     // staging for the inputs and the output after the s_W scratch.  The
     // tensor-core form reads D only through its band trapezoids, so it stages
@@ -772,7 +889,7 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     }
     if (ctx->profiling) CK(cudaEventRecord(tev[2], cs), "record last segment");
     // the staged label buffer is 256-byte aligned: re-plan so the direct path can be taken
-    rc = layout_for(ctx, L.form, n, n4, base + lab_off, label_type, K, P, &L);
+    rc = layout_for(ctx, L.plan, n, n4, base + lab_off, label_type, K, P, &L);
     if (rc) return rc;
     SWProblem pr{reinterpret_cast<const float*>(dmat), n, n4, base + lab_off, label_type, K,
                  P, nullptr, reinterpret_cast<double*>(base + out_off)};
@@ -867,11 +984,20 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     // batch is processed in form order.  Every per-row result is independent
     // of the other rows in its launch and of the padded group count, so each
     // test's s_W, F and p equal those of the same test run alone.
-    std::vector<int> form(T);
-    for (uint32_t t = 0; t < T; ++t) form[t] = plan_form(ctx, n, Ks[t], Ps[t] + 1);
+    // tests are grouped by their whole plan (form and knobs: every knob that
+    // changes the arithmetic is the same for the tests of one launch)
+    std::vector<Plan> plans;
+    std::vector<uint32_t> pid(T);
+    for (uint32_t t = 0; t < T; ++t) {
+        const Plan pl = plan_for(ctx, n, Ks[t], Ps[t] + 1);
+        uint32_t k = 0;
+        while (k < plans.size() && !(plans[k] == pl)) ++k;
+        if (k == plans.size()) plans.push_back(pl);
+        pid[t] = k;
+    }
     std::vector<uint32_t> order(T);
     for (uint32_t t = 0; t < T; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return form[x] < form[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return pid[x] < pid[y]; });
     std::vector<uint64_t> rs(T + 1, 0);      // row starts in form order
     std::vector<uint32_t> ks(T);
     std::vector<uint64_t> sd(T);
@@ -884,15 +1010,15 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     const int lt = Kmax <= 256 ? LABEL_U8 : Kmax <= 65536 ? LABEL_U16 : LABEL_I32;
     // form groups [gb[q], gb[q+1]) of the ordered tests, each with its own
     // weight table (stride = the group's n_groups) and row starts
-    struct FormGroup { uint32_t t0, t1, K; int form; size_t w_off, rs_off; };
+    struct FormGroup { uint32_t t0, t1, K; Plan plan; size_t w_off, rs_off; };
     std::vector<FormGroup> groups;
     std::vector<double> gw;
     std::vector<uint64_t> grs;
     for (uint32_t k = 0; k < T;) {
         uint32_t e = k;
         uint32_t Kg = 0;
-        while (e < T && form[order[e]] == form[order[k]]) Kg = std::max(Kg, ks[e++]);
-        FormGroup fg{k, e, Kg, form[order[k]], gw.size(), grs.size()};
+        while (e < T && pid[order[e]] == pid[order[k]]) Kg = std::max(Kg, ks[e++]);
+        FormGroup fg{k, e, Kg, plans[pid[order[k]]], gw.size(), grs.size()};
         for (uint32_t q = k; q < e; ++q)
             for (uint32_t c = 0; c < Kg; ++c) gw.push_back(hw[(size_t)order[q] * Kmax + c]);
         for (uint32_t q = k; q <= e; ++q) grs.push_back(rs[q] - rs[k]);
@@ -902,7 +1028,7 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     size_t sw_scratch = 0;
     for (const FormGroup& fg : groups) {
         SWLayout L;
-        int rc = layout_for(ctx, fg.form, n, ld, nullptr, lt, fg.K, rs[fg.t1] - rs[fg.t0], &L);
+        int rc = layout_for(ctx, fg.plan, n, ld, nullptr, lt, fg.K, rs[fg.t1] - rs[fg.t0], &L);
         if (rc) return rc;
         sw_scratch = std::max(sw_scratch, L.total);
     }
@@ -911,7 +1037,7 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
     off = align_up(off + (size_t)n * rows * label_bytes(lt));
     const size_t sw_off = off;
     off = align_up(off + (size_t)rows * sizeof(double));
-    const uint32_t chunks = brute_chunks(n, ctx->sm_count);
+    const uint32_t chunks = brute_chunks(n, ctx->sm_count, 1);
     const size_t st_off = off;
     off = align_up(off + (size_t)(chunks + 1) * sizeof(double));
     const size_t w_off = off;
@@ -958,7 +1084,7 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
         const uint64_t r0 = rs[fg.t0], nr = rs[fg.t1] - r0;
         void* glab = static_cast<char*>(labels) + (size_t)n * r0 * label_bytes(lt);
         SWLayout L;
-        rc = layout_for(ctx, fg.form, n, ld, glab, lt, fg.K, nr, &L);
+        rc = layout_for(ctx, fg.plan, n, ld, glab, lt, fg.K, nr, &L);
         if (rc) return rc;
         SWProblem pr{mat, n, ld, glab, lt, fg.K, nr, dw + fg.w_off, sW + r0};
         pr.w_row_start = dgrs + fg.rs_off;

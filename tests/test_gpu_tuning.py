@@ -87,3 +87,56 @@ def test_graph_replay_matches_direct_launches(ctx):
         np.testing.assert_allclose(out.cpu().numpy(), ref2, rtol=1e-5)
     finally:
         pm.permanova_set_graphs(ctx.handle, False)
+
+
+@pytest.mark.parametrize("plan", [
+    dict(form=pm.FORM_BRUTE, brute_chunk_mult=2),
+    dict(form=pm.FORM_PERMBLOCK, permblock_variant=0),
+    dict(form=pm.FORM_PERMBLOCK, permblock_variant=1),
+    dict(form=pm.FORM_GEMM, gemm_rows_div=2, gemm_drain_kblocks=8),
+    dict(form=pm.FORM_GEMM, gemm_rows_div=4, gemm_drain_kblocks=4),
+    dict(form=pm.FORM_GEMM, gemm_rows_div=1, gemm_drain_kblocks=3),
+], ids=["brute-x2", "pb-pair", "pb-f32", "gemm-half-8", "gemm-quarter-4", "gemm-full-3"])
+@pytest.mark.parametrize("n,K,P", [(1001, 4, 300), (2500, 3, 257), (640, 40, 130)])
+def test_every_plan_matches_oracle(ctx, plan, n, K, P):
+    """Every knob setting the autotuner can pick gives s_W within the stated
+    tolerance of the FP64 oracle (sizes with ragged tiles and label-row
+    blocks; K = 40 exceeds the tensor-core form's usual range but runs)."""
+    D, rows, w = _case(n, K, P, n + K)
+    Dd, lab, wd = (torch.from_numpy(D).cuda(), torch.from_numpy(rows.astype(np.uint8)).cuda(),
+                   torch.from_numpy(w).cuda())
+    pm.permanova_set_plan(ctx.handle, **plan)
+    try:
+        desc = pm.permanova_plan_describe(ctx.handle, n, K, P)
+        assert desc["source"] == "forced"
+        out = ctx.sW(Dd, lab, K, wd)
+        pm.permanova_sync(ctx.handle)
+    finally:
+        pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5)
+
+
+def test_plan_knob_limits(ctx):
+    with pytest.raises(pm.PermanovaError) as ei:
+        pm.permanova_set_plan(ctx.handle, pm.FORM_GEMM, gemm_drain_kblocks=16)
+    assert ei.value.status == pm.EINVAL and "accuracy" in str(ei.value)
+    with pytest.raises(pm.PermanovaError):
+        pm.permanova_set_plan(ctx.handle, pm.FORM_PERMBLOCK, permblock_variant=2)
+    pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
+
+
+def test_autotuned_plan_is_described_and_matches_oracle(ctx):
+    """After permanova_autotune the bucket's plan (form and knobs) is the
+    autotuned one, and calls in that bucket match the oracle."""
+    n, K, P = 1500, 6, 600
+    D, rows, w = _case(n, K, P, 9)
+    Dd, lab, wd = (torch.from_numpy(D).cuda(), torch.from_numpy(rows.astype(np.uint8)).cuda(),
+                   torch.from_numpy(w).cuda())
+    form = pm.permanova_autotune(ctx.handle, Dd, n, n, lab, pm.LABEL_U8, K, P, wd)
+    desc = pm.permanova_plan_describe(ctx.handle, n, K, P)
+    assert desc["source"] == "autotuned" and desc["form"] == pm.FORM_NAMES[form]
+    out = ctx.sW(Dd, lab, K, wd)
+    pm.permanova_sync(ctx.handle)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5)

@@ -457,8 +457,9 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
 
 // ---------------------------------------------------------------------------
 // label blocks: for label-row tile q (ppt rows) and k-block kb (64 columns),
-// one contiguous block of ppt x 64 uint8 labels, blocks ordered (q, kb);
-// rows beyond P and columns beyond n hold 0.  Labels >= K raise DEV_BAD_LABEL
+// one contiguous block of ppt x 64 uint8 labels, blocks ordered (q, kb), each
+// label row's four 16-byte chunks XOR-swizzled (chunk c at position
+// c ^ ((row / 2) % 4)); rows beyond P and columns beyond n hold 0.  Labels >= K raise DEV_BAD_LABEL
 // and are clamped to K-1.
 // ---------------------------------------------------------------------------
 template <typename Lin>
@@ -482,7 +483,10 @@ __global__ void k_repack_gemm(const Lin* __restrict__ in, uint32_t n, uint64_t P
                     lab = K - 1;
                 }
             }
-            dst[e] = (uint8_t)lab;
+            // 16-byte chunk c of label row pl is stored at chunk position
+            // c ^ ((pl / 2) % 4): the builders then read the same logical chunk
+            // of up to 8 label rows from 8 distinct bank groups
+            dst[pl * g::BK + (((c >> 4) ^ ((pl >> 1) & 3u)) << 4) + (c & 15u)] = (uint8_t)lab;
         }
     }
 }
@@ -801,7 +805,8 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                 for (uint32_t idx = et; idx < 2 * per_half; idx += 128) {
                     const uint32_t h = idx / per_half, rem = idx - h * per_half;
                     const uint32_t p = rem / (g::BK / 16), c16 = rem % (g::BK / 16);
-                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(lb + h * lab_bytes + p * g::BK + c16 * 16));
+                    const uint32_t phys = c16 ^ ((p >> 1) & 3u);   // swizzled chunk position
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(lb + h * lab_bytes + p * g::BK + phys * 16));
                     *reinterpret_cast<uint4*>(lab_rows + p * g::BM + h * g::BK + c16 * 16) = v;
                 }
                 mbar_arrive(epi_bar);
@@ -933,16 +938,23 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             const uint32_t pl = t / halfk, g0 = 2 * (t - pl * halfk);
             const bool busy = pl < a.ppt;
             const uint32_t row0 = pl * K + g0;
-            const uint32_t key0 = (0x4300u | g0) * 0x00010001u, key1 = (0x4300u | (g0 + 1)) * 0x00010001u;
+            // Thread t builds rows 2t and 2t + 1.  Lanes 0-3 of each group of 8
+            // store row 2t first, lanes 4-7 row 2t + 1 first, so every store
+            // instruction's 8-lane phase writes rows of 8 distinct residues mod
+            // 8 at one chunk index: 8 distinct bank groups of the swizzled tile.
+            // Label chunk q is read from its swizzled position (conflict-free).
+            const bool swap = (t & 4u) != 0;
+            const uint32_t rowA = row0 + (swap ? 1u : 0u), rowB = row0 + (swap ? 0u : 1u);
+            const uint32_t key0 = (0x4300u | (g0 + (swap ? 1u : 0u))) * 0x00010001u;   // row A's group
+            const uint32_t key1 = (0x4300u | (g0 + (swap ? 0u : 1u))) * 0x00010001u;   // row B's group
             uint32_t loff[4], s0[8], s1[8];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
-                loff[q] = pl * g::BK + ch * 16;
-                s0[2 * q] = sw128_offset(row0, 2 * ch);
-                s0[2 * q + 1] = sw128_offset(row0, 2 * ch + 1);
-                s1[2 * q] = sw128_offset(row0 + 1, 2 * ch);
-                s1[2 * q + 1] = sw128_offset(row0 + 1, 2 * ch + 1);
+                loff[q] = pl * g::BK + ((((uint32_t)q) ^ ((pl >> 1) & 3u)) << 4);
+                s0[2 * q] = sw128_offset(rowA, 2 * q);
+                s0[2 * q + 1] = sw128_offset(rowA, 2 * q + 1);
+                s1[2 * q] = sw128_offset(rowB, 2 * q);
+                s1[2 * q + 1] = sw128_offset(rowB, 2 * q + 1);
             }
             Ring rb, rl;
             bool ok = true;
@@ -993,16 +1005,17 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         } else {
         const uint32_t pl = c / K, gg = c - pl * K;
         const uint32_t key = (0x4300u | gg) * 0x00010001u;   // (0x43gg, 0x43gg)
-        // the row's label chunk offsets in a label slice and its B-row store
-        // offsets in a B tile, the same for every k-block: chunk (q + pl/2) % 4
-        // at step q puts the up to 8 label rows a warp reads on distinct banks
+        // the row's label chunk offsets in a label slice (chunk q at its
+        // swizzled position: the up to 8 label rows a warp reads sit on
+        // distinct banks) and its B-row store offsets in a B tile (chunk 2q + h
+        // of 8 consecutive rows: 8 distinct bank groups), the same for every
+        // k-block
         uint32_t loff[4], soff[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t ch = ((uint32_t)q + (pl >> 1)) & 3u;
-            loff[q] = pl * g::BK + ch * 16;
-            soff[2 * q] = sw128_offset(c, 2 * ch);
-            soff[2 * q + 1] = sw128_offset(c, 2 * ch + 1);
+            loff[q] = pl * g::BK + ((((uint32_t)q) ^ ((pl >> 1) & 3u)) << 4);
+            soff[2 * q] = sw128_offset(c, 2 * q);
+            soff[2 * q + 1] = sw128_offset(c, 2 * q + 1);
         }
         Ring rb, rl;
         bool ok = true;

@@ -175,6 +175,8 @@ struct GemmPlan {
     uint64_t plane_elems;  // bf16 elements per plane (hi or lo) of the banded upper triangle
 };
 bool gemm_available();
+// work counters in the GEMM scratch: one per launch of a call (at most this many)
+constexpr uint32_t kGemmWorkCounters = 32;
 // ppt_div > 1 divides the label rows per tile (narrower MMA tiles, more work
 // units per band)
 GemmPlan gemm_plan(uint32_t n, uint32_t K, uint64_t P, uint32_t ppt_div = 1);
@@ -190,10 +192,15 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
                              uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu);
 // the tensor-core kernel over bands [I0, I1): partials is gp.n_bands x P, this
 // launch writes the rows of its bands
-// drain_kb: k-blocks accumulated in tensor memory between FP64 drains (0 = default)
+// drain_kb: k-blocks accumulated in tensor memory between FP64 drains (0 =
+// default); counter: which of the scratch's work counters the launch takes its
+// units from (zeroed by the caller, on the launch's stream, before it runs)
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu, uint32_t drain_kb = 0);
+                             uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu, uint32_t drain_kb = 0,
+                             uint32_t counter = 0);
+// the kGemmWorkCounters work counters inside a GEMM scratch
+unsigned long long* gemm_work_counters(const GemmPlan& gp, void* scratch);
 
 // a bounded wait on an mbarrier that never completes (failure-detection self-test)
 cudaError_t launch_wait_selftest(DevStatus* st, long long limit_cycles, cudaStream_t s);

@@ -70,6 +70,8 @@ constexpr int NBS = 2;              // one-hot B-tile stages (built on chip)
 constexpr int DRAIN_KB = 8;         // default k-blocks per accumulator chunk
 constexpr int PREFETCH_KB = 8;      // L2 prefetch distance along the band (k-blocks)
 constexpr int THREADS = 512;        // 16 warps
+constexpr uint32_t UQ = 32;         // unit ring slots (work units fetched ahead, power of 2)
+constexpr uint32_t UQ_CONSUMERS = 13;   // unit-ring readers: MMA thread, 4 epilogue and 8 builder warps
 constexpr int BUILDERS = 256;       // warps 8-15: one B row per thread
 constexpr uint32_t PLANE_BYTES = BM * BK * 2;             // 16 KB
 constexpr uint32_t TILE_BYTES = 2 * PLANE_BYTES;          // hi + lo planes: 32 KB
@@ -86,9 +88,10 @@ constexpr uint32_t OFF_LABROWS = OFF_LRING + LRING_BYTES;          // [PPT_MAX][
 constexpr uint32_t OFF_ACC64 = OFF_LABROWS;                        // [4][NMAX] double
 constexpr uint32_t UNIT_BYTES = PPT_MAX * BM > 4 * NMAX * 8 ? PPT_MAX * BM : 4 * NMAX * 8;
 constexpr uint32_t OFF_BAR = OFF_LABROWS + UNIT_BYTES;
-constexpr uint32_t N_BARS = 2 * NA + 2 * NBS + 2 * NL_MAX + 6;
+constexpr uint32_t N_BARS = 2 * NA + 2 * NBS + 2 * NL_MAX + 6 + 2 * UQ;
 constexpr uint32_t OFF_MISC = OFF_BAR + N_BARS * 8;
-constexpr uint32_t SMEM_BYTES = OFF_MISC + 16;
+constexpr uint32_t OFF_UQ = OFF_MISC + 16;                 // [UQ] unit ids
+constexpr uint32_t SMEM_BYTES = OFF_UQ + UQ * 8;
 constexpr uint32_t SMEM_ALLOC = SMEM_BYTES + 1024;       // room to align the base to 1 KB
 constexpr long long WAIT_LIMIT = 4000000000LL;           // clock cycles (~2 s)
 static_assert(SMEM_ALLOC <= 232448, "shared memory budget");
@@ -305,8 +308,18 @@ static size_t tile_bytes_total(const GemmPlan& gp) {
     return (size_t)(nb * (nb + 1)) * g::TILE_BYTES;
 }
 
+// after the tiles: two 32-bit words per band, then the work counters of the
+// launches of one call (one per launch, zeroed before the first)
+static size_t work_counter_offset(const GemmPlan& gp) {
+    return (tile_bytes_total(gp) + 2 * (size_t)gp.n_bands * sizeof(uint32_t) + 7) / 8 * 8;
+}
+
 size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
-    return tile_bytes_total(gp) + 2 * (size_t)gp.n_bands * sizeof(uint32_t);
+    return work_counter_offset(gp) + kGemmWorkCounters * sizeof(unsigned long long);
+}
+
+unsigned long long* gemm_work_counters(const GemmPlan& gp, void* scratch) {
+    return reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(scratch) + work_counter_offset(gp));
 }
 
 // ---------------------------------------------------------------------------
@@ -543,6 +556,7 @@ struct GemmArgs {
     uint32_t N;                // MMA N (multiple of 16, <= 256)
     uint32_t drain_kb;         // k-blocks accumulated in TMEM between drains
     uint32_t I0, I1;           // bands [I0, I1) of this launch
+    unsigned long long* work;  // the launch's work counter (zero at launch): next unit to hand out
 };
 
 // Bounded wait.  With `obey_abort` the wait also gives up once another role
@@ -607,6 +621,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     uint64_t* acc_empty = acc_full + 2;             // [2]
     uint64_t* epi_bar = acc_full + 4;               // epilogue warps meet here 2 or 4 times per unit
     uint64_t* mma_done = acc_full + 5;              // final commit of the MMA thread
+    uint64_t* uq_full = acc_full + 6;               // [UQ] unit id published
+    uint64_t* uq_empty = uq_full + g::UQ;           // [UQ] unit id read by every consumer
+    volatile unsigned long long* uq = reinterpret_cast<volatile unsigned long long*>(sm + g::OFF_UQ);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + g::OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + g::OFF_MISC + 4);
     uint8_t* lring = sm + g::OFF_LRING;                          // [NL][ppt][64] labels
@@ -643,6 +660,10 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         }
         mbar_init(epi_bar, 128);
         mbar_init(mma_done, 1);
+        for (uint32_t k = 0; k < g::UQ; ++k) {
+            mbar_init(&uq_full[k], 1);
+            mbar_init(&uq_empty[k], g::UQ_CONSUMERS);
+        }
         *abort_flag = (st->code != DEV_OK) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -659,9 +680,32 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // units (band I0 + u / n_ptiles, label-row tile u % n_ptiles) of this launch's band range
+    // Work units (band I0 + u / n_ptiles, label-row tile u % n_ptiles) of this
+    // launch's band range, in band-major order.  They form the launch's work
+    // queue: the producer takes the next unit from the work counter whenever
+    // its label stream starts one (so a CTA that finishes early takes more
+    // work, and the CTAs running together stay on neighbouring units of a band)
+    // and publishes it in the unit ring; every role reads the ring in order.
+    // A unit id of ~0 ends the queue.  Every ring wait is bounded.
     const uint64_t n_units = (uint64_t)(a.I1 - a.I0) * a.n_ptiles;
     const uint32_t NB = 2 * a.n_bands;
+    constexpr unsigned long long END = ~0ull;
+    // a consumer's next unit: position pos of the ring (all lanes of the warp
+    // wait; the outcome is warp-uniform; lane 0 releases the slot)
+    auto next_unit = [&](uint64_t pos, bool whole_warp, unsigned where, bool& okv) -> unsigned long long {
+        const uint32_t slot = (uint32_t)(pos & (g::UQ - 1));
+        const uint32_t par = (uint32_t)((pos / g::UQ) & 1);
+        const bool got = whole_warp ? lanes_wait(&uq_full[slot], par, abort_flag, st, where)
+                                    : wait_bar(&uq_full[slot], par, abort_flag, st, where);
+        if (!got) {
+            okv = false;
+            return END;
+        }
+        const unsigned long long u = uq[slot];
+        if (whole_warp) __syncwarp();
+        if (!whole_warp || lane == 0) mbar_arrive(&uq_empty[slot]);
+        return u;
+    };
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -672,10 +716,30 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             uint64_t kc = 0;                 // A stream position
             uint64_t lk = 0;                 // label stream position
             Ring ra, rl;                     // A ring and label ring slots
-            uint64_t lu = blockIdx.x;        // label stream unit and k-block
-            uint32_t lkb = lu < n_units ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
             bool ok = true;
-            for (uint64_t u = blockIdx.x; u < n_units && ok && !*abort_flag; u += gridDim.x) {
+            uint64_t pub = 0;                // units published in the unit ring
+            // take the next unit from the work counter and publish it (END once the
+            // queue is empty); a slot is reused once every consumer has read it
+            auto publish = [&]() -> unsigned long long {
+                const uint32_t slot = (uint32_t)(pub & (g::UQ - 1));
+                if (!wait_bar(&uq_empty[slot], (uint32_t)((pub / g::UQ) & 1) ^ 1, abort_flag, st, 19)) {
+                    ok = false;
+                    return END;
+                }
+                unsigned long long u = atomicAdd(a.work, 1ull);
+                if (u >= n_units) u = END;
+                uq[slot] = u;
+                mbar_arrive(&uq_full[slot]);
+                ++pub;
+                return u;
+            };
+            unsigned long long lu = publish();   // label stream unit and k-block
+            uint32_t lkb = lu != END ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
+            for (uint64_t apos = 0; ok && !*abort_flag; ++apos) {
+                // the A stream's unit: published by the label stream, which runs ahead
+                // (by fewer than UQ units, so the slot still holds it)
+                const unsigned long long u = uq[apos & (g::UQ - 1)];
+                if (u == END) break;
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint8_t* tile = a.tiles + tiles_before_band(I, NB) * (uint64_t)g::TILE_BYTES;
                 for (uint32_t kb = 2 * I; kb < NB; ++kb, ++kc, tile += g::TILE_BYTES) {
@@ -683,7 +747,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                     // kc + NL - 1, and (waiting if need be) up to position kc before A tile
                     // kc; a slot frees only when the builders are done with it, so waiting
                     // for one further ahead would hold back the A copies
-                    while (lu < n_units && lk < kc + NL) {
+                    while (lu != END && lk < kc + NL) {
                         if (lk > kc) {
                             if (!mbar_test(&lempty[rl.idx], rl.phase ^ 1)) break;
                         } else if (!wait_bar(&lempty[rl.idx], rl.phase ^ 1, abort_flag, st, 12)) {
@@ -697,8 +761,8 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
                         ++lk;
                         rl.next(NL);
                         if (++lkb == NB) {
-                            lu += gridDim.x;
-                            lkb = lu < n_units ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
+                            lu = publish();
+                            lkb = lu != END ? 2 * (a.I0 + (uint32_t)(lu / a.n_ptiles)) : 0;
                         }
                     }
                     if (!ok) break;
@@ -727,7 +791,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             uint64_t cc = 0;
             Ring ra, rb;
             bool ok = true;
-            for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            for (uint64_t pos = 0; ok; ++pos) {
+                const unsigned long long u = next_unit(pos, false, 20, ok);
+                if (u == END) break;
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint32_t nkb = NB - 2 * I;
                 // the band's lo plane is FP16, or BF16 where its range is too wide
@@ -786,7 +852,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         uint64_t cc = 0;
         uint32_t epi_phase = 0;
         bool ok = true;
-        for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        for (uint64_t pos = 0; ok; ++pos) {
+            const unsigned long long u = next_unit(pos, true, 21, ok);
+            if (u == END) break;
             const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint64_t p0 = (u % a.n_ptiles) * a.ppt;
             const uint32_t nlab = (uint32_t)min((uint64_t)a.ppt, a.P - p0);
@@ -959,7 +1027,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
             Ring rb, rl;
             bool ok = true;
             uint32_t seq = 0;   // k-blocks of this CTA so far: stage seq % 2
-            for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            for (uint64_t pos = 0; ok; ++pos) {
+                const unsigned long long u = next_unit(pos, true, 22, ok);
+                if (u == END) break;
                 const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
                 const uint32_t nkb = NB - 2 * I;
                 for (uint32_t k = 0; k < nkb; ++k, ++seq) {
@@ -1019,7 +1089,9 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         }
         Ring rb, rl;
         bool ok = true;
-        for (uint64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        for (uint64_t pos = 0; ok; ++pos) {
+            const unsigned long long u = next_unit(pos, true, 22, ok);
+            if (u == END) break;
             const uint32_t I = a.I0 + (uint32_t)(u / a.n_ptiles);
             const uint32_t nkb = NB - 2 * I;
             for (uint32_t k = 0; k < nkb; ++k) {
@@ -1076,7 +1148,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0, uint32_t I1, uint32_t drain_kb) {
+                             uint32_t I0, uint32_t I1, uint32_t drain_kb, uint32_t counter) {
     if (I1 > gp.n_bands) I1 = gp.n_bands;
     if (I0 >= I1) return cudaSuccess;
     GemmArgs a;
@@ -1096,6 +1168,8 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
     a.I0 = I0;
     a.I1 = I1;
+    if (counter >= kGemmWorkCounters) return cudaErrorInvalidValue;
+    a.work = gemm_work_counters(gp, const_cast<void*>(scratch)) + counter;
     // accumulation length in TMEM between FP64 drains: the plan's, else the
     // default (the environment variable overrides both; accuracy studies only)
     a.drain_kb = drain_kb ? drain_kb : (uint32_t)g::DRAIN_KB;

@@ -366,8 +366,10 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
         } else {
             const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P, L.plan.gemm_ppt_div);
             void* gs = base + L.gemm_off;
+            unsigned long long* counters = gemm_work_counters(gp, gs);
             if (!arr) {
                 CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
+                CK(cudaMemsetAsync(counters, 0, sizeof(unsigned long long), s), "reset the work counter");
                 int rc = profile_begin(ctx, s);
                 if (rc) return rc;
                 CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s, 0, 0xFFFFFFFFu,
@@ -380,6 +382,10 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                 // band words and partial rows), so a segment's last wave overlaps the
                 // next segment's first; s2 starts after everything queued on s so far
                 // and s continues after all of s2's work
+                // one work counter per segment launch, all zeroed before the fork
+                if (arr->band.size() - 1 > kGemmWorkCounters) return fail(PERMANOVA_EINVAL, "too many segments");
+                CK(cudaMemsetAsync(counters, 0, (arr->band.size() - 1) * sizeof(unsigned long long), s),
+                   "reset the work counters");
                 CK(cudaEventRecord(arr->fork, s), "fork segment streams");
                 CK(cudaStreamWaitEvent(arr->s2, arr->fork, 0), "fork segment streams");
                 for (size_t k = 0; k + 1 < arr->band.size(); ++k) {
@@ -388,7 +394,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                     CK(launch_gemm_prep(q, gp, gs, sk, arr->band[k], arr->band[k + 1]),
                        "GEMM operand preparation");
                     CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, sk, arr->band[k],
-                                        arr->band[k + 1], L.plan.gemm_drain),
+                                        arr->band[k + 1], L.plan.gemm_drain, (uint32_t)k),
                        "GEMM kernel");
                 }
                 CK(cudaEventRecord(arr->join, arr->s2), "join segment streams");

@@ -337,14 +337,16 @@ def forms_compare(pk: dict, reps: int = 3) -> dict:
 
 
 def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
-                seed: int = 5005) -> dict:
+                seed: int = 5005, burst_tests: int = 600) -> dict:
     """Serving workload: 64 resident matrices (n log-uniform in 500..30,000,
     Gaussian points in R^16/R^32, Euclidean fp32), each with 1-20 categorical
     factors (K uniform in 2..12, Dirichlet(2) sizes, each group >= 2), tests of
     999 or 9,999 permutations (even odds) arriving as a Poisson process at
     ``rate`` tests/s.  Arrivals during the first ``warmup_s`` seconds are
     served but not counted; tests/s and p50/p99 latency (arrival to result)
-    are taken over the ``duration`` seconds after that."""
+    are taken over the ``duration`` seconds after that.  Then ``burst_tests``
+    tests of the same mix are submitted at once: completed tests / time to the
+    last result is the server's capacity."""
     import torch
     import paper_2505_04556_gb300 as pm
     from paper_2505_04556_gb300.serve import Request, Server
@@ -388,6 +390,19 @@ def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
         r.done.wait(600)
     t_meas = t0 + warmup_s
     wall = max(r.t_done for r in measured) - t_meas
+    # capacity: a burst of tests from the same mix submitted at once, timed
+    # from the first submission to the last result (the server saturated)
+    burst = []
+    tb = time.perf_counter()
+    for j in range(burst_tests):
+        m = int(rng.integers(64))
+        lab, K = factors[m][int(rng.integers(len(factors[m])))]
+        P = 999 if rng.random() < 0.5 else 9999
+        burst.append(srv.submit(Request(m, lab, K, P, seed=50_000 + j)))
+    for r in burst:
+        r.done.wait(600)
+    burst_wall = max(r.t_done for r in burst) - tb
+    burst_ok = sum(r.error is None for r in burst)
     srv.close()
     s = Server.summarize(measured, wall)
     evals = sum(mats[r.matrix_id].shape[0] * (mats[r.matrix_id].shape[0] - 1) / 2 * (r.n_perms + 1)
@@ -397,6 +412,8 @@ def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
            "tests": s.get("tests"), "errors": s.get("errors"), "offered_rate": rate,
            "duration_s": duration, "warmup_s": warmup_s, "slots": slots,
            "mean_batch": s.get("mean_batch"), "pair_perm_evals_per_s": evals / wall,
+           "capacity_tests_per_s": burst_ok / burst_wall, "capacity_burst": burst_tests,
+           "capacity_mean_batch": float(np.mean([r.batch_size for r in burst])),
            "matrices_resident": len(mats), "resident_gb": round(resident / 1e9, 1),
            "config": {"workload": "serving-64", "matrices": 64, "n_range": [500, 30000],
                       "perms": [999, 9999], "K_range": [2, 12], "factors_per_matrix": [1, 20],

@@ -116,7 +116,8 @@ int permanova_set_form(permanova_ctx *ctx, int form);
 /* A kernel plan: the form and its knobs (0 = the default of a knob). */
 typedef struct {
     int form;                     /* permanova_form_t; AUTO restores the planner */
-    int permblock_variant;        /* 0: paired FP16-compare kernel for uint8 codes, 1: FP32 compare-and-set */
+    int permblock_variant;        /* 0: paired FP16-compare kernel for uint8 codes (3 blocks/SM),
+                                     2: the same at 4 blocks/SM, 1: FP32 compare-and-set */
     uint32_t gemm_rows_div;       /* tensor-core form: label rows per tile divided by 1, 2 or 4 */
     uint32_t gemm_drain_kblocks;  /* tensor-core form: k-blocks between FP64 drains, 1 .. 8 (default 8) */
     uint32_t brute_chunk_mult;    /* brute force: chunks per label row multiplied by 1 .. 16 */
@@ -141,8 +142,8 @@ int permanova_plan_describe(permanova_ctx *ctx, uint32_t n_dims, uint32_t n_grou
  * planner's choice for calls with the same log2 buckets of n_dims and n_perms
  * and the same n_groups.  The candidates cover every form that can run these
  * sizes and each form's knobs: the brute force's chunks per label row (x1,
- * x2), the perm-block kernel's variant (paired FP16 compares or FP32
- * compare-and-set), the tensor-core form's label rows per tile (full or
+ * x2), the perm-block kernel's variant (paired FP16 compares at 3 or 4
+ * blocks per SM, or FP32 compare-and-set), the tensor-core form's label rows per tile (full or
  * half width) and drain interval (8 or 4 k-blocks: never longer, the accuracy
  * limit of the 1e-5 target).  Arguments as permanova_sW (no output buffer:
  * the sample's results go to scratch).  *out_form (optional, HOST) receives

@@ -59,18 +59,20 @@ struct WeightMap {
     const uint64_t* row_start;  // DEVICE, n_sets + 1 ascending row offsets, or NULL
     uint32_t n_sets;
     uint32_t K;                 // weights per set
-    // The K weights label row p uses.
-    __device__ __forceinline__ const double* row(uint64_t p) const {
+    // Index of the weight set label row p uses.
+    __device__ __forceinline__ uint64_t set_of(uint64_t p) const {
         if (row_start) {
             uint32_t lo = 0, hi = n_sets - 1;   // last set whose first row is <= p
             while (lo < hi) {
                 const uint32_t mid = (lo + hi + 1) / 2;
                 if (__ldg(row_start + mid) <= p) lo = mid; else hi = mid - 1;
             }
-            return w + (uint64_t)lo * K;
+            return lo;
         }
-        return set_rows ? w + (p / set_rows) * K : w;
+        return set_rows ? p / set_rows : 0;
     }
+    // The K weights label row p uses.
+    __device__ __forceinline__ const double* row(uint64_t p) const { return w + set_of(p) * K; }
 };
 
 struct SWProblem {

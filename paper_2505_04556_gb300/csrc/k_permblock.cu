@@ -196,12 +196,15 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
 // compare-and-set.  Row segments are summed in FP32 (two chains per label
 // row), weighted once per row segment (Algorithm 2) in FP32 into an 8-row
 // group sum, and group sums are added in FP64, as in the kernel above.  The
-// weights are read per row from the (L1-resident) weight table.
+// weight sets of the CTA's label rows are staged once as an FP32 table in
+// shared memory (the launcher uses this kernel only when they fit), so the
+// FP64 pipe sees no per-row work.
 // ---------------------------------------------------------------------------
 constexpr int PB2_THREADS = 128;              // threads per CTA
 constexpr int PB2_ROWS = 2 * PB2_THREADS;     // label rows per CTA
 constexpr uint32_t PB2_LAB_BYTES = PB_T * PB2_THREADS * 2;   // row labels of p and p': 16 KB
-constexpr uint32_t pb2_smem_bytes() { return PB_D2_BYTES + PB2_LAB_BYTES; }
+constexpr uint32_t PB2_WTAB = 2048;                          // FP32 weights staged per CTA (8 KB)
+constexpr uint32_t pb2_smem_bytes() { return PB_D2_BYTES + PB2_LAB_BYTES + PB2_WTAB * 4; }
 
 // acc0 += d where the low FP16 halves of a and b are equal, acc1 += d where
 // the high halves are.
@@ -212,8 +215,8 @@ __device__ __forceinline__ void pair_add(float& acc0, float& acc1, uint32_t a, u
         : "r"(a), "r"(b), "f"(d));
 }
 
-template <bool VEC>
-__global__ void __launch_bounds__(PB2_THREADS, 4)
+template <bool VEC, int MINB>
+__global__ void __launch_bounds__(PB2_THREADS, MINB)
 k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
                     const uint8_t* __restrict__ labels, uint64_t lstride, uint64_t P, const WeightMap wm,
                     uint32_t K, uint32_t n_pblocks, double* __restrict__ partials,
@@ -234,8 +237,17 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
     const uint64_t ra = act_a ? pa : P - 1, rb = act_b ? pb : P - 1;
     const uint8_t* ga = labels + ra * lstride;
     const uint8_t* gb = labels + rb * lstride;
-    const double* wa = wm.row(ra);
-    const double* wb = wm.row(rb);
+    // the weight sets of the CTA's label rows as an FP32 table in shared memory
+    float* wtab = reinterpret_cast<float*>(pb_smem + PB_D2_BYTES + PB2_LAB_BYTES);
+    const uint64_t p_first = (uint64_t)q * PB2_ROWS, p_last = min(P, p_first + PB2_ROWS) - 1;
+    const uint64_t set_lo = wm.set_of(p_first);
+    const uint64_t n_sets_cta = wm.set_of(p_last) - set_lo + 1;
+    // (the launcher takes this kernel only when every CTA's sets fit the table)
+    for (uint32_t e = threadIdx.x; e < n_sets_cta * K; e += PB2_THREADS)
+        wtab[e] = (float)__ldg(wm.w + set_lo * K + e);
+    // the two rows' weight sets as shared-memory addresses (one register each)
+    const uint32_t wsa = (uint32_t)__cvta_generic_to_shared(wtab + (wm.set_of(ra) - set_lo) * K);
+    const uint32_t wsb = (uint32_t)__cvta_generic_to_shared(wtab + (wm.set_of(rb) - set_lo) * K);
     const uint32_t r0 = band * PB_T;
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     for (uint32_t r = 0; r < rows; ++r) {
@@ -316,8 +328,11 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
                     pair_add(a1, b1, cl[4 * c4 + 3], key, dv.w);
                 }
                 // each row segment weighted once (Algorithm 2)
-                grp_a = fmaf(a0 + a1, (float)__ldg(wa + (lab & 0xFFu)), grp_a);
-                grp_b = fmaf(b0 + b1, (float)__ldg(wb + (lab >> 8)), grp_b);
+                float w_a, w_b;
+                asm("ld.shared.f32 %0, [%1];" : "=f"(w_a) : "r"(wsa + ((lab & 0xFFu) << 2)));
+                asm("ld.shared.f32 %0, [%1];" : "=f"(w_b) : "r"(wsb + ((lab >> 8) << 2)));
+                grp_a = fmaf(a0 + a1, w_a, grp_a);
+                grp_b = fmaf(b0 + b1, w_b, grp_b);
             }
             tot_a += (double)grp_a;
             tot_b += (double)grp_b;
@@ -354,6 +369,10 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
     return launched(1);
 }
 
+// minb: CTAs per SM the register budget is sized for (3: 168 registers a
+// thread, the default, measured 0.87-0.91 of the issue roofline at n = 20k;
+// 4: 128 registers, more warps but spills, 0.81-0.86)
+template <int MINB>
 static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double* partials,
                                   const DevStatus* st, cudaStream_t s) {
     const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
@@ -362,17 +381,18 @@ static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double*
     const uint64_t blocks = (uint64_t)n_bands * n_pblocks;
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     const uint32_t smem = pb2_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock_pair<true, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sw_permblock_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sw_permblock_pair<false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e != cudaSuccess) return e;
     if (vec)
-        k_sw_permblock_pair<true><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+        k_sw_permblock_pair<true, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
             pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     else
-        k_sw_permblock_pair<false><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+        k_sw_permblock_pair<false, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
             pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     return launched(1);
@@ -381,13 +401,23 @@ static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double*
 // pr.labels must be uint8 (pr.label_type == LABEL_U8) or uint16 codes with a
 // row stride of lstride elements, lstride * sizeof(code) a multiple of 16 and
 // the base address 16-byte aligned.  variant 0: the paired FP16-compare
-// kernel for uint8 codes (the FP32 compare-and-set kernel for uint16);
-// variant 1: the FP32 compare-and-set kernel for both.
+// kernel for uint8 codes whose weight sets fit its FP32 table (else, and for
+// uint16 codes, the FP32 compare-and-set kernel), sized for 3 CTAs per SM;
+// variant 2: the same paired kernel sized for 4 CTAs per SM; variant 1: the
+// FP32 compare-and-set kernel.
 cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
                                       const DevStatus* st, cudaStream_t s, int variant) {
-    if (pr.label_type == LABEL_U8)
-        return variant == 0 ? launch_pb_pair(pr, lstride, partials, st, s)
-                            : launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
+    if (pr.label_type == LABEL_U8) {
+        // weight sets a CTA of the paired kernel can meet: one, a run of equal
+        // sets, or (ragged sets) at most all of them
+        const WeightMap wm = pr.weights();
+        const uint64_t sets = wm.row_start ? wm.n_sets
+                              : wm.set_rows ? (PB2_ROWS + wm.set_rows - 1) / wm.set_rows + 1 : 1;
+        const bool fits = sets * pr.K <= PB2_WTAB;
+        if (fits && variant == 0) return launch_pb_pair<3>(pr, lstride, partials, st, s);
+        if (fits && variant == 2) return launch_pb_pair<4>(pr, lstride, partials, st, s);
+        return launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
+    }
     return launch_pb_t<uint16_t>(pr, lstride, partials, st, s);
 }
 

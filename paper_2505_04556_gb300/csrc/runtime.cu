@@ -33,7 +33,8 @@ int log2_bucket(uint64_t x) {
 // A kernel plan: the form and the knobs of that form.
 struct Plan {
     int form = PERMANOVA_FORM_BRUTE;
-    int pb_variant = 0;          // perm-block: 0 paired FP16 compares (uint8 codes), 1 FP32 compare-and-set
+    int pb_variant = 0;          // perm-block: 0 paired FP16 compares (uint8 codes, 3 CTAs/SM), 2 the
+                                 // same at 4 CTAs/SM, 1 FP32 compare-and-set
     uint32_t gemm_ppt_div = 1;   // tensor-core form: label rows per tile divided by this
     uint32_t gemm_drain = 0;     // tensor-core form: k-blocks between FP64 drains (0 = default, 8)
     uint32_t brute_mult = 1;     // brute force: chunks per label row multiplied by this
@@ -498,8 +499,8 @@ int permanova_set_plan(permanova_ctx* ctx, const permanova_plan_t* plan) {
     }
     if (plan->form < PERMANOVA_FORM_BRUTE || plan->form > PERMANOVA_FORM_GEMM)
         return fail(PERMANOVA_EINVAL, "unknown form %d", plan->form);
-    if (plan->permblock_variant < 0 || plan->permblock_variant > 1)
-        return fail(PERMANOVA_EINVAL, "perm-block variant must be 0 or 1");
+    if (plan->permblock_variant < 0 || plan->permblock_variant > 2)
+        return fail(PERMANOVA_EINVAL, "perm-block variant must be 0, 1 or 2");
     if (plan->gemm_rows_div != 0 && plan->gemm_rows_div != 1 && plan->gemm_rows_div != 2 &&
         plan->gemm_rows_div != 4)
         return fail(PERMANOVA_EINVAL, "gemm_rows_div must be 1, 2 or 4");
@@ -657,8 +658,8 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
         pl.brute_mult = mult;
         cands.push_back(pl);
     }
-    for (int var : {0, 1}) {
-        if (var == 0 && K > 256) continue;
+    for (int var : {0, 2, 1}) {
+        if (var != 1 && K > 256) continue;
         Plan pl = plan_of_form(PERMANOVA_FORM_PERMBLOCK);
         pl.pb_variant = var;
         cands.push_back(pl);
@@ -724,11 +725,13 @@ int permanova_plan_describe(permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t
                      src, gp.perms_per_tile, (gp.perms_per_tile * K + 15) / 16 * 16,
                      pl.gemm_drain ? pl.gemm_drain : 8u);
     } else if (pl.form == PERMANOVA_FORM_PERMBLOCK) {
-        const bool pair = pl.pb_variant == 0 && K <= 256;
+        const bool pair = pl.pb_variant != 1 && K <= 256;
         m = snprintf(out, cap,
                      "{\"form\": \"permblock\", \"source\": \"%s\", \"variant\": \"%s\", "
                      "\"label_rows_per_block\": %u, \"tile\": 64}",
-                     src, pair ? "paired f16x2 compare" : "f32 compare-and-set", pair ? 256u : 128u);
+                     src, !pair ? "f32 compare-and-set" : pl.pb_variant == 2 ? "paired f16x2 compare, 4 CTAs/SM"
+                                                                          : "paired f16x2 compare, 3 CTAs/SM",
+                     pair ? 256u : 128u);
     } else {
         m = snprintf(out, cap, "{\"form\": \"brute\", \"source\": \"%s\", \"chunks_per_row\": %u}", src,
                      brute_chunks(n, ctx->sm_count, pl.brute_mult));

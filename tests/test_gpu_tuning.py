@@ -93,10 +93,11 @@ def test_graph_replay_matches_direct_launches(ctx):
     dict(form=pm.FORM_BRUTE, brute_chunk_mult=2),
     dict(form=pm.FORM_PERMBLOCK, permblock_variant=0),
     dict(form=pm.FORM_PERMBLOCK, permblock_variant=1),
+    dict(form=pm.FORM_PERMBLOCK, permblock_variant=2),
     dict(form=pm.FORM_GEMM, gemm_rows_div=2, gemm_drain_kblocks=8),
     dict(form=pm.FORM_GEMM, gemm_rows_div=4, gemm_drain_kblocks=4),
     dict(form=pm.FORM_GEMM, gemm_rows_div=1, gemm_drain_kblocks=3),
-], ids=["brute-x2", "pb-pair", "pb-f32", "gemm-half-8", "gemm-quarter-4", "gemm-full-3"])
+], ids=["brute-x2", "pb-pair", "pb-f32", "pb-pair3", "gemm-half-8", "gemm-quarter-4", "gemm-full-3"])
 @pytest.mark.parametrize("n,K,P", [(1001, 4, 300), (2500, 3, 257), (640, 40, 130)])
 def test_every_plan_matches_oracle(ctx, plan, n, K, P):
     """Every knob setting the autotuner can pick gives s_W within the stated
@@ -122,7 +123,7 @@ def test_plan_knob_limits(ctx):
         pm.permanova_set_plan(ctx.handle, pm.FORM_GEMM, gemm_drain_kblocks=16)
     assert ei.value.status == pm.EINVAL and "accuracy" in str(ei.value)
     with pytest.raises(pm.PermanovaError):
-        pm.permanova_set_plan(ctx.handle, pm.FORM_PERMBLOCK, permblock_variant=2)
+        pm.permanova_set_plan(ctx.handle, pm.FORM_PERMBLOCK, permblock_variant=3)
     pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
 
 

@@ -247,9 +247,12 @@ def roofline(form: str, K: int, evals_per_launch: float, kernel_ms: float, pk: d
             "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"] + " (copy)"}
 
 
-def traffic_per_launch(form: str, evals: float) -> float | None:
+def traffic_per_launch(form: str, evals: float, workload: str | None = None) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (bytes per pair-perm evaluation x evaluations)."""
+    the current kernel source and (when the record names one) on this
+    workload: bytes per pair-perm evaluation x evaluations.  The bytes per
+    evaluation of the cached forms depend on n (L2 reuse), so a record is
+    only applied to the workload it was measured on."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -259,6 +262,8 @@ def traffic_per_launch(form: str, evals: float) -> float | None:
     for line in open(path):
         kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
         if kv.get("form") == form and kv.get("src_sha") == sha and "bytes_per_eval" in kv:
+            if workload is not None and kv.get("workload", workload) != workload:
+                continue
             return float(kv["bytes_per_eval"]) * evals
     return None
 
@@ -587,7 +592,7 @@ def main():
     evals_per_launch = pairs * rows_done / launches
     pk = peaks()
     rl = roofline(form, K, evals_per_launch, kernel_ms, pk,
-                  traffic_per_launch(form, evals_per_launch))
+                  traffic_per_launch(form, evals_per_launch, args.workload))
     rl["kernel_ms"] = kernel_ms
 
     # ---- end to end through the host entry point ----

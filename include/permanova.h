@@ -69,7 +69,9 @@ typedef enum {
  *   BRUTE      Algorithm 3's brute force: the triangle is streamed from HBM
  *              once per label row (HBM-bound).
  *   PERMBLOCK  a triangle tile of D^2 is held in shared memory and reused by
- *              a block of 128 label rows (CUDA-core, issue-bound); the row
+ *              a block of 256 label rows, two per thread compared at once
+ *              with packed FP16 equality (uint8 codes; 128 rows with FP32
+ *              compares for uint16 codes), CUDA-core and issue-bound; the row
  *              weight is applied once per row segment as in Algorithm 2.
  *   GEMM       the dense-contraction form Z_p = (D o D) X_p with one-hot
  *              indicator columns X_p, on the tcgen05 tensor cores: D^2, scaled
@@ -78,7 +80,7 @@ typedef enum {
  *              accumulation in tensor memory drained every 512 columns, FP64
  *              partial sums.  Needs n_groups <= 256.
  *   AUTO       the planner's choice for (n, K, P): a bucket timed by
- *              permanova_autotune if there is one, else GEMM for K <= 32,
+ *              permanova_autotune if there is one, else GEMM for K <= 24,
  *              n >= 256 and P >= 32, else PERMBLOCK for P >= 16, else BRUTE.
  * Accuracy of s_W against an FP64 evaluation of the definition: the CUDA-core
  * forms (BRUTE, PERMBLOCK) sum in FP32 per row segment and FP64 beyond, about

@@ -145,10 +145,11 @@ Plan plan_for(const permanova_ctx* ctx, uint32_t n, uint32_t K, uint64_t P) {
     auto it = ctx->tuned.find(TuneKey{log2_bucket(n), K, log2_bucket(P)});
     if (it != ctx->tuned.end()) return it->second;
     // The tensor-core form costs 4K flops per pair and label row (two 16-bit
-    // planes, K one-hot columns); the CUDA-core forms about 2 instructions.
-    // Measured on a GB300 at n = 20,000 with 4,000 label rows: the GEMM form is
-    // 2.22x the perm-block form at K = 16, 1.11x at K = 32 and 0.85x at K = 40.
-    if (gemm_available() && K <= 32 && n >= 256 && P >= 32) pl.form = PERMANOVA_FORM_GEMM;
+    // planes, K one-hot columns); the paired perm-block kernel about 1.6
+    // instructions per pair and label row whatever K is.  Measured on a GB300
+    // at n = 20,000 with 4,000 label rows: GEMM / perm-block = 1.62 at K = 16,
+    // 1.22 at 20, 1.10 at 22, 1.01 at 24, 0.90 at 26, 0.78 at 32.
+    if (gemm_available() && K <= 24 && n >= 256 && P >= 32) pl.form = PERMANOVA_FORM_GEMM;
     else if (P >= 16 && K <= 65536) pl.form = PERMANOVA_FORM_PERMBLOCK;
     else pl.form = PERMANOVA_FORM_BRUTE;
     return pl;

@@ -63,3 +63,14 @@ def test_traffic_record_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_per_launch("gemm", 1e12) is None
 
+
+
+def test_traffic_record_applies_only_to_its_workload(tmp_path, monkeypatch):
+    sha = _tree(tmp_path, "// kernel\n", None)
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        f"form=gemm src_sha={sha} bytes_per_eval=1.0e-02 workload=euclid-100k read_GB=1\n"
+        f"form=gemm src_sha={sha} bytes_per_eval=3.0e-03 workload=euclid-20k read_GB=1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_per_launch("gemm", 1e12, "euclid-100k") == pytest.approx(1.0e10)
+    assert bench.traffic_per_launch("gemm", 1e12, "euclid-20k") == pytest.approx(3.0e9)
+    assert bench.traffic_per_launch("gemm", 1e12, "jaccard-25k") is None

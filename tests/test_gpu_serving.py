@@ -154,7 +154,7 @@ def test_oversized_request_rejected_not_run(matrices):
 def test_mixed_batch_equals_single_tests(matrices):
     """Tests on one matrix with different group counts and permutation counts,
     run through one permanova_test_mixed call (one s_W pass per kernel form:
-    here the tensor-core form for K <= 32, the perm-block form for K = 40 and
+    here the tensor-core form for K <= 24, the perm-block form for K = 40 and
     the brute force for 9 permutations), equal the same tests run one by one
     bit for bit, and their s_W rows land in caller order."""
     import paper_2505_04556_gb300 as pm

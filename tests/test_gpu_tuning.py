@@ -32,10 +32,10 @@ def _case(n, K, P, seed):
 
 
 def test_planner_boundary(ctx):
-    """Without a tuned bucket the planner takes the GEMM form up to 32 groups
-    and the perm-block form from 33 (measured crossover at n = 20k)."""
-    assert pm.permanova_plan_form(ctx.handle, 20000, 32, 4000) == pm.FORM_GEMM
-    assert pm.permanova_plan_form(ctx.handle, 20000, 33, 4000) == pm.FORM_PERMBLOCK
+    """Without a tuned bucket the planner takes the GEMM form up to 24 groups
+    and the perm-block form from 25 (measured crossover at n = 20k)."""
+    assert pm.permanova_plan_form(ctx.handle, 20000, 24, 4000) == pm.FORM_GEMM
+    assert pm.permanova_plan_form(ctx.handle, 20000, 25, 4000) == pm.FORM_PERMBLOCK
 
 
 def test_autotune_then_auto_plan(ctx):

@@ -28,7 +28,9 @@ test's sizes), so a test gives bit-identical s_W, F and p alone, batched and
 among other traffic.
 
 Latency is measured from arrival (submit) to completion; the server reports
-tests/s and p50/p99 latency.
+tests/s and p50/p99 latency.  With ``max_pending`` set, a request that finds
+that many requests already waiting is refused at once ("server busy"), so
+the latency of admitted requests stays bounded under overload.
 """
 from __future__ import annotations
 
@@ -117,10 +119,12 @@ class Server:
     """``matrices``: dict id -> square fp32 CUDA tensor (resident)."""
 
     def __init__(self, matrices: dict, n_slots: int = 4, hbm_budget_bytes: int = 0,
-                 device: int = 0, max_batch: int = 16, reserve_per_slot: int = 0):
+                 device: int = 0, max_batch: int = 16, reserve_per_slot: int = 0,
+                 max_pending: int = 0):
         import torch
         self.torch = torch
         self.max_batch = max_batch
+        self.max_pending = max_pending    # 0: unbounded; else requests beyond it are refused
         self.device = device
         self.matrices = matrices
         free, _ = torch.cuda.mem_get_info(device)
@@ -172,6 +176,12 @@ class Server:
             return req
         req._need = need
         with self.cv:
+            if self.max_pending and len(self.pending) >= self.max_pending:
+                # back-pressure: the caller learns at once that the server is full
+                req.error = f"server busy: {len(self.pending)} requests waiting (limit {self.max_pending})"
+                req.t_done = time.perf_counter()
+                req.done.set()
+                return req
             self.pending.append(req)
             self.cv.notify_all()
         return req

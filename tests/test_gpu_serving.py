@@ -219,3 +219,22 @@ def test_server_fuses_different_group_and_permutation_counts(matrices):
     assert max(r.batch_size for r in mixed) > 1
     for r, ref in zip(mixed, alone):
         assert r.result == ref
+
+
+def test_back_pressure_refuses_beyond_the_waiting_limit(matrices):
+    """With max_pending set, requests that find the waiting queue full are
+    refused at once with a "server busy" error; admitted ones complete."""
+    from paper_2505_04556_gb300.serve import Request, Server
+    mats, hosts = matrices
+    n = hosts[2].shape[0]
+    srv = Server(mats, n_slots=1, max_pending=2)
+    try:
+        reqs = [srv.submit(Request(2, synth.observed_labels([n // 2, n - n // 2], 80 + k), 2, 999,
+                                   seed=700 + k)) for k in range(12)]
+        for r in reqs:
+            assert r.done.wait(120)
+    finally:
+        srv.close()
+    busy = [r for r in reqs if r.error and "server busy" in r.error]
+    served = [r for r in reqs if r.error is None]
+    assert busy and served and len(busy) + len(served) == len(reqs)

@@ -212,19 +212,18 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
 /* Same as permanova_sW with HOST buffers: mat (n_dims x ld fp32),
  * groupings, inv_group_sizes and out_sW live in host memory (pinned memory
  * gives full copy speed).  The call copies the inputs to the device, runs
- * s_W, copies the n_perms results back and synchronises `stream`.  Only the
- * part of mat that s_W reads is copied: for each 128-row band, rows
- * [128 b, 128 b + 128) from column 128 b on (about half of the matrix); with
- * the tensor-core form only those band trapezoids are staged on the device
- * (context scratch of about half the matrix), else a full-width copy.  The
- * copies run on a stream of the context, ordered after the work already queued
- * on `stream`; with the tensor-core form the bands are copied in up to 16
- * segments and each segment's kernels start as soon as it has landed, so the
- * copies overlap the computation.  Segments alternate between `stream` and a
- * second stream of the context (joined back into `stream` before the final
- * reduction), so one segment's last wave of blocks overlaps the next
- * segment's first.  Errors as permanova_sW, plus any error the device
- * reported (the call synchronises). */
+ * s_W, copies the n_perms results back and synchronises `stream`.  All copies
+ * are flat (one-dimensional).  With the tensor-core form each 128-row band b
+ * is copied as the host range from element (128 b, 128 b) to the end of the
+ * band's last row, in up to 16 segments through three device staging slots
+ * of about a sixteenth of the matrix each, and each segment's kernels start
+ * as soon as it has landed, so the copies overlap the computation; segments
+ * alternate between `stream` and a second stream of the context (joined back
+ * into `stream` before the final reduction), so one segment's last wave of
+ * blocks overlaps the next segment's first.  The CUDA-core forms copy the
+ * whole matrix first.  The copies run on a stream of the context, ordered
+ * after the work already queued on `stream`.  Errors as permanova_sW, plus
+ * any error the device reported (the call synchronises). */
 int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
                       const void *groupings, int label_type, uint32_t n_groups, uint64_t n_perms,
                       const float *inv_group_sizes, double *out_sW, void *stream);
@@ -369,6 +368,41 @@ int permanova_test_mixed(permanova_ctx *ctx, const float *mat, uint32_t n_dims, 
                          const int32_t *groupings, uint32_t n_tests, const uint32_t *n_groups,
                          const uint64_t *n_perms, const uint64_t *seeds, permanova_result *out_host,
                          double *out_sW, void *stream);
+
+/* A prepared matrix: the tensor-core form's operands (D^2 of every band
+ * trapezoid, scaled per band and split into the BF16 hi and FP16/BF16 lo
+ * tiles, with the band words) made once and reused by every call that names
+ * it, so a run of many batches (the 13 batches of a 99,999-permutation test
+ * at n = 100,000) or the many tests of a served matrix pay for them once.
+ * Not a paper operation: the paper recomputes nothing between permutations
+ * because its kernel reads D directly.
+ *   permanova_prepare   mat (DEVICE, as in permanova_sW) is read once, on
+ *                       `stream`, into a new device allocation of about
+ *                       2 n^2 bytes owned by the handle (not counted in any
+ *                       context's budget); synchronises `stream`.  The
+ *                       caller keeps mat alive and unchanged while the handle
+ *                       exists (calls whose plan is a CUDA-core form read it).
+ *                       *out is NULL on failure (EINVAL, ENOMEM, ECUDA).
+ *   permanova_prepared_destroy   waits for the device and frees the handle.
+ * The handle is read-only after preparation: contexts on its device may use
+ * it concurrently. */
+typedef struct permanova_prepared permanova_prepared;
+int permanova_prepare(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t ld,
+                      permanova_prepared **out, void *stream);
+void permanova_prepared_destroy(permanova_prepared *prepared);
+
+/* permanova_sW on a prepared matrix: the same arguments after the handle,
+ * the same results bit for bit; with the tensor-core form the operand
+ * preparation is skipped (and its scratch not needed). */
+int permanova_sW_prepared(permanova_ctx *ctx, const permanova_prepared *prepared, const void *groupings,
+                          int label_type, uint32_t n_groups, uint64_t n_perms,
+                          const float *inv_group_sizes, double *out_sW, void *stream);
+
+/* permanova_test_mixed on a prepared matrix (same results bit for bit). */
+int permanova_test_mixed_prepared(permanova_ctx *ctx, const permanova_prepared *prepared,
+                                  const int32_t *groupings, uint32_t n_tests, const uint32_t *n_groups,
+                                  const uint64_t *n_perms, const uint64_t *seeds,
+                                  permanova_result *out_host, double *out_sW, void *stream);
 
 #ifdef __cplusplus
 }

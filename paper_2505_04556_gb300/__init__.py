@@ -130,6 +130,15 @@ def load(path: str | None = None):
         lib.permanova_test_mixed.argtypes = [vp, vp, u32, u64, vp, u32, vp, vp, vp,
                                              ctypes.POINTER(permanova_result), vp, vp]
         lib.permanova_test_mixed.restype = i32
+        lib.permanova_prepare.argtypes = [vp, vp, u32, u64, ctypes.POINTER(vp), vp]
+        lib.permanova_prepare.restype = i32
+        lib.permanova_prepared_destroy.argtypes = [vp]
+        lib.permanova_prepared_destroy.restype = None
+        lib.permanova_sW_prepared.argtypes = [vp, vp, vp, i32, u32, u64, vp, vp, vp]
+        lib.permanova_sW_prepared.restype = i32
+        lib.permanova_test_mixed_prepared.argtypes = [vp, vp, vp, u32, vp, vp, vp,
+                                                      ctypes.POINTER(permanova_result), vp, vp]
+        lib.permanova_test_mixed_prepared.restype = i32
         lib.permanova_selftest_wait.argtypes = [vp, u32, vp]
         lib.permanova_selftest_wait.restype = i32
         lib.permanova_set_graphs.argtypes = [vp, i32]
@@ -298,6 +307,40 @@ def permanova_test_mixed(ctx, mat, n_dims: int, ld: int, groupings, n_groups, n_
                                      ctypes.cast(ks, ctypes.c_void_p), ctypes.cast(ps, ctypes.c_void_p),
                                      ctypes.cast(sd, ctypes.c_void_p), res, _ptr(out_sW),
                                      _stream(stream))
+    _check(ctx, rc)
+    return [r.as_dict() for r in res]
+
+
+def permanova_prepare(ctx, mat, n_dims: int, ld: int, stream=None):
+    h = ctypes.c_void_p()
+    rc = load().permanova_prepare(ctx, _ptr(mat), int(n_dims), int(ld), ctypes.byref(h), _stream(stream))
+    _check(ctx, rc)
+    return h.value
+
+
+def permanova_prepared_destroy(prepared) -> None:
+    load().permanova_prepared_destroy(prepared)
+
+
+def permanova_sW_prepared(ctx, prepared, groupings, label_type: int, n_groups: int, n_perms: int,
+                          inv_group_sizes, out_sW, stream=None) -> None:
+    rc = load().permanova_sW_prepared(ctx, prepared, _ptr(groupings), int(label_type), int(n_groups),
+                                      int(n_perms), _ptr(inv_group_sizes), _ptr(out_sW), _stream(stream))
+    _check(ctx, rc)
+
+
+def permanova_test_mixed_prepared(ctx, prepared, groupings, n_groups, n_perms, seeds, out_sW=None,
+                                  stream=None) -> list:
+    T = len(seeds)
+    res = (permanova_result * T)()
+    ks = (ctypes.c_uint32 * T)(*[int(k) for k in n_groups])
+    ps = (ctypes.c_uint64 * T)(*[int(p) for p in n_perms])
+    sd = (ctypes.c_uint64 * T)(*[int(x) & (2**64 - 1) for x in seeds])
+    rc = load().permanova_test_mixed_prepared(ctx, prepared, _ptr(groupings), T,
+                                              ctypes.cast(ks, ctypes.c_void_p),
+                                              ctypes.cast(ps, ctypes.c_void_p),
+                                              ctypes.cast(sd, ctypes.c_void_p), res, _ptr(out_sW),
+                                              _stream(stream))
     _check(ctx, rc)
     return [r.as_dict() for r in res]
 

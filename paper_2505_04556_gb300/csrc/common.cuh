@@ -88,9 +88,10 @@ struct SWProblem {
     // Weight sets: 0 = one set of K weights for every label row; otherwise
     // label row p uses w[(p / w_set_rows) * K + g] (several tests in one pass).
     uint64_t w_set_rows;
-    // Layout of mat: 0 = row-major with row stride ld; 1 = band trapezoids
-    // (see band_trapezoid_offset; tensor-core form only, ld unused).
+    // Layout of mat: 0 = row-major with row stride ld; 1 = band-flat (see
+    // band_flat_offset; tensor-core form only), holding bands [band0, ...).
     uint32_t banded;
+    uint32_t band0;
     // Ragged weight sets (override w_set_rows): set t covers label rows
     // [w_row_start[t], w_row_start[t+1]) (DEVICE, w_sets + 1 entries).
     const uint64_t* w_row_start;
@@ -100,28 +101,29 @@ struct SWProblem {
     }
 };
 
-// Band-trapezoid layout of the strict upper triangle (the host entry point's
-// staging of D for the tensor-core form): band I holds rows [128 I, 128 I + 128)
-// from column 128 I on, with row stride n4 - 128 I (n4 = n rounded up to 4),
-// bands stored back to back.  Offset (in floats) of band I's first element:
-// 128 * sum_{I' < I} (n4 - 128 I').
-__host__ __device__ __forceinline__ uint64_t band_trapezoid_offset(uint64_t I, uint64_t n4) {
-    return 128ull * (I * n4 - (I ? 64ull * I * (I - 1) : 0ull));
+// Band-flat layout (the host entry point's staging of D for the tensor-core
+// form): band I (rows [128 I, 128 I + 128)) is the contiguous range of the
+// row-major n x ld matrix from element (128 I, 128 I) to the end of the band's
+// last row, ((rows - 1) ld + n - 128 I) floats, which one flat copy moves;
+// the bands of a staging slot are stored back to back.  Offset (in floats) of
+// band I's first element from band 0's: sum_{I' < I} (127 ld + n - 128 I').
+__host__ __device__ __forceinline__ uint64_t band_flat_offset(uint64_t I, uint64_t ld, uint64_t n) {
+    return I * (127ull * ld + n) - (I ? 64ull * I * (I - 1) : 0ull);
 }
-// Total floats of the layout for n objects.
-__host__ __device__ __forceinline__ uint64_t band_trapezoid_floats(uint32_t n) {
-    const uint64_t n4 = (n + 3ull) / 4 * 4, nb = (n + 127ull) / 128, last = nb - 1;
-    const uint64_t rows_last = n - 128ull * last;
-    return band_trapezoid_offset(last, n4) + rows_last * (n4 - 128ull * last);
+// Floats of band I in that layout (the last band may have fewer rows).
+__host__ __device__ __forceinline__ uint64_t band_flat_floats(uint64_t I, uint64_t ld, uint64_t n) {
+    const uint64_t r0 = 128ull * I, rows = n - r0 < 128ull ? n - r0 : 128ull;
+    return (rows - 1) * ld + (n - r0);
 }
-// Address of element (i, 0) of row i in either layout (only elements j >=
-// 128 * (i / 128) of a band-trapezoid row exist; the address itself may lie
+// Address of element (i, 0) of row i in either layout (in the band-flat one
+// only elements j >= 128 * (i / 128) exist, and the address itself may lie
 // before the row's first stored element).
 __host__ __device__ __forceinline__ const float* d_row(const float* mat, uint64_t ld, uint32_t banded,
-                                                       uint32_t n, uint32_t i) {
+                                                       uint32_t n, uint32_t i, uint32_t band0 = 0) {
     if (!banded) return mat + (uint64_t)i * ld;
-    const uint64_t n4 = (n + 3ull) / 4 * 4, I = i >> 7;
-    return mat + band_trapezoid_offset(I, n4) + (uint64_t)(i - 128 * I) * (n4 - 128 * I) - 128 * I;
+    const uint64_t I = i >> 7;
+    return mat + (band_flat_offset(I, ld, n) - band_flat_offset(band0, ld, n)) + (uint64_t)(i - 128 * I) * ld -
+           128 * I;
 }
 
 // inv_group_sizes (fp32, the paper's input) -> FP64 copy used by the kernels
@@ -177,7 +179,7 @@ struct GemmPlan {
     uint64_t plane_elems;  // bf16 elements per plane (hi or lo) of the banded upper triangle
 };
 bool gemm_available();
-// work counters in the GEMM scratch: one per launch of a call (at most this many)
+// work counters of one call's GEMM launches (one per launch, at most this many)
 constexpr uint32_t kGemmWorkCounters = 32;
 // ppt_div > 1 divides the label rows per tile (narrower MMA tiles, more work
 // units per band)
@@ -195,14 +197,11 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
 // the tensor-core kernel over bands [I0, I1): partials is gp.n_bands x P, this
 // launch writes the rows of its bands
 // drain_kb: k-blocks accumulated in tensor memory between FP64 drains (0 =
-// default); counter: which of the scratch's work counters the launch takes its
-// units from (zeroed by the caller, on the launch's stream, before it runs)
+// default); work: the launch's work counter (DEVICE, zeroed by the caller on
+// the launch's stream before it runs), from which the kernel takes its units
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0 = 0, uint32_t I1 = 0xFFFFFFFFu, uint32_t drain_kb = 0,
-                             uint32_t counter = 0);
-// the kGemmWorkCounters work counters inside a GEMM scratch
-unsigned long long* gemm_work_counters(const GemmPlan& gp, void* scratch);
+                             uint32_t I0, uint32_t I1, uint32_t drain_kb, unsigned long long* work);
 
 // a bounded wait on an mbarrier that never completes (failure-detection self-test)
 cudaError_t launch_wait_selftest(DevStatus* st, long long limit_cycles, cudaStream_t s);

@@ -308,18 +308,10 @@ static size_t tile_bytes_total(const GemmPlan& gp) {
     return (size_t)(nb * (nb + 1)) * g::TILE_BYTES;
 }
 
-// after the tiles: two 32-bit words per band, then the work counters of the
-// launches of one call (one per launch, zeroed before the first)
-static size_t work_counter_offset(const GemmPlan& gp) {
-    return (tile_bytes_total(gp) + 2 * (size_t)gp.n_bands * sizeof(uint32_t) + 7) / 8 * 8;
-}
-
+// the prepared operands: the tiles, then two 32-bit words per band (they
+// depend on D alone, not on the label rows)
 size_t gemm_scratch_bytes(const GemmPlan& gp, uint64_t) {
-    return work_counter_offset(gp) + kGemmWorkCounters * sizeof(unsigned long long);
-}
-
-unsigned long long* gemm_work_counters(const GemmPlan& gp, void* scratch) {
-    return reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(scratch) + work_counter_offset(gp));
+    return tile_bytes_total(gp) + 2 * (size_t)gp.n_bands * sizeof(uint32_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -340,12 +332,13 @@ __device__ __forceinline__ void tile_coords(uint64_t t, uint32_t n_bands, uint32
 
 // d^2 of the 8 entries (i, j0 .. j0+7) in FP32, zero outside the strict upper
 // triangle (j <= i, i >= n or j >= n).  D is row-major (stride ld) or in the
-// band-trapezoid layout (banded); j0 >= 128 * (i / 128) in both.
+// band-flat layout starting at band band0 (banded); j0 >= 128 * (i / 128).
 __device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t n, uint64_t ld,
-                                         uint32_t banded, bool vec, bool diag, uint32_t i, uint32_t j0,
+                                         uint32_t banded, uint32_t band0, bool vec, bool diag, uint32_t i,
+                                         uint32_t j0,
                                          float (&x)[8]) {
     float v[8];
-    const float* row = i < n ? d_row(mat, ld, banded, n, i) : mat;
+    const float* row = i < n ? d_row(mat, ld, banded, n, i, band0) : mat;
     if (i < n && vec && !diag && j0 + 7 < n) {
         const float4* src = reinterpret_cast<const float4*>(row + j0);
         const float4 a = __ldg(src), b = __ldg(src + 1);
@@ -370,7 +363,8 @@ __device__ __forceinline__ void squared8(const float* __restrict__ mat, uint32_t
 // non-negative floats (bit order = value order), into bmax[I] (zeroed
 // beforehand) and bmin[I] (set to all ones beforehand).
 __global__ void __launch_bounds__(256)
-k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t n_bands, bool vec,
+k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t band0,
+                uint32_t n_bands, bool vec,
                 uint64_t t0, uint64_t t1, uint32_t* __restrict__ bmax, uint32_t* __restrict__ bmin) {
     __shared__ uint32_t wmax[8], wmin[8];
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
@@ -380,7 +374,7 @@ k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t
         uint32_t m = 0, mn = 0xFFFFFFFFu;
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             float x[8];
-            squared8(mat, n, ld, banded, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
+            squared8(mat, n, ld, banded, band0, vec, diag, I * g::BM + (job >> 3), kb * g::BK + (job & 7) * 8, x);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const uint32_t b = __float_as_uint(x[e]);
@@ -410,7 +404,8 @@ k_gemm_band_max(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t
 }
 
 __global__ void __launch_bounds__(256)
-k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t n_bands, bool vec,
+k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t banded, uint32_t band0,
+            uint32_t n_bands, bool vec,
             uint64_t t0, uint64_t t1, uint8_t* __restrict__ tiles, const uint32_t* __restrict__ bmax,
             const uint32_t* __restrict__ bmin) {
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
@@ -423,7 +418,7 @@ k_gemm_prep(const float* __restrict__ mat, uint32_t n, uint64_t ld, uint32_t ban
         for (int job = threadIdx.x; job < g::BM * 8; job += blockDim.x) {
             const uint32_t r = job >> 3, c8 = job & 7;
             float x[8];
-            squared8(mat, n, ld, banded, vec, diag, I * g::BM + r, kb * g::BK + c8 * 8, x);
+            squared8(mat, n, ld, banded, band0, vec, diag, I * g::BM + r, kb * g::BK + c8 * 8, x);
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
@@ -450,9 +445,9 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
                              uint32_t I0, uint32_t I1) {
     if (I1 > gp.n_bands) I1 = gp.n_bands;
     if (I0 >= I1) return cudaSuccess;
-    // a band-trapezoid D has 16-byte aligned rows (every offset and stride a
-    // multiple of 4 floats) whenever its base is
-    const bool vec = (pr.banded || pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
+    // a band-flat D has 16-byte aligned rows when ld and n are multiples of 4
+    // (every band offset and row offset then is) and its base is aligned
+    const bool vec = (pr.ld % 4 == 0) && (!pr.banded || pr.n % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
     const uint64_t NB = 2ull * gp.n_bands;
     const uint64_t t0 = tiles_before_band(I0, NB), t1 = tiles_before_band(I1, NB);
     const uint64_t n_tiles = t1 - t0;
@@ -463,8 +458,10 @@ cudaError_t launch_gemm_prep(const SWProblem& pr, const GemmPlan& gp, void* scra
     cudaError_t e = cudaMemsetAsync(bmax + I0, 0, (size_t)(I1 - I0) * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bmin + I0, 0xFF, (size_t)(I1 - I0) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, gp.n_bands, vec, t0, t1, bmax, bmin);
-    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, gp.n_bands, vec, t0, t1, tiles, bmax, bmin);
+    k_gemm_band_max<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, pr.band0, gp.n_bands, vec, t0, t1,
+                                           bmax, bmin);
+    k_gemm_prep<<<blocks, 256, 0, s>>>(pr.mat, pr.n, pr.ld, pr.banded, pr.band0, gp.n_bands, vec, t0, t1, tiles,
+                                       bmax, bmin);
     return launched(2);
 }
 
@@ -1148,7 +1145,7 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
 
 cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void* scratch,
                              double* partials, DevStatus* st, int sm_count, cudaStream_t s,
-                             uint32_t I0, uint32_t I1, uint32_t drain_kb, uint32_t counter) {
+                             uint32_t I0, uint32_t I1, uint32_t drain_kb, unsigned long long* work) {
     if (I1 > gp.n_bands) I1 = gp.n_bands;
     if (I0 >= I1) return cudaSuccess;
     GemmArgs a;
@@ -1168,8 +1165,8 @@ cudaError_t launch_gemm_main(const SWProblem& pr, const GemmPlan& gp, const void
     if (a.N > (uint32_t)g::NMAX) a.N = g::NMAX;
     a.I0 = I0;
     a.I1 = I1;
-    if (counter >= kGemmWorkCounters) return cudaErrorInvalidValue;
-    a.work = gemm_work_counters(gp, const_cast<void*>(scratch)) + counter;
+    if (!work) return cudaErrorInvalidValue;
+    a.work = work;
     // accumulation length in TMEM between FP64 drains: the plan's, else the
     // default (the environment variable overrides both; accuracy studies only)
     a.drain_kb = drain_kb ? drain_kb : (uint32_t)g::DRAIN_KB;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <array>
+#include <functional>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +40,7 @@ struct Plan {
     uint32_t gemm_drain = 0;     // tensor-core form: k-blocks between FP64 drains (0 = default, 8)
     uint32_t brute_mult = 1;     // brute force: chunks per label row multiplied by this
     bool tuned = false;
+    bool prepared = false;       // GEMM operands come from a prepared matrix (no scratch for them)
     bool operator==(const Plan& o) const {
         return form == o.form && pb_variant == o.pb_variant && gemm_ppt_div == o.gemm_ppt_div &&
                gemm_drain == o.gemm_drain && brute_mult == o.brute_mult;
@@ -81,6 +83,17 @@ struct permanova_ctx {
     cudaEvent_t seg_fork = nullptr, seg_join = nullptr;
 };
 
+// A matrix whose tensor-core operands (the split D^2 tiles and band words)
+// were made once and are reused by every call that names it.
+struct permanova_prepared {
+    int device = 0;
+    const float* mat = nullptr;   // the caller's matrix (the CUDA-core forms still read it)
+    uint32_t n = 0;
+    uint64_t ld = 0;
+    void* ops = nullptr;
+    size_t bytes = 0;
+};
+
 namespace {
 
 thread_local std::string tl_err;
@@ -120,6 +133,7 @@ struct DeviceGuard {
 
 constexpr size_t kAlign = 256;
 constexpr uint32_t kHostSegments = 16;   // band segments of the host entry point's copy pipeline
+constexpr uint32_t kHostSlots = 3;       // staging slots of the tensor-core form's band segments
 size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 // Scratch carve-up for one s_W call.
@@ -132,7 +146,8 @@ struct SWLayout {
     int code_type = LABEL_U8;
     uint64_t lstride = 0;
     size_t lab_off = 0;
-    size_t gemm_off = 0;
+    size_t gemm_off = 0;        // prepared operands (GEMM form; unused when prepared elsewhere)
+    size_t counter_off = 0;     // GEMM work counters
     size_t w_off = 0;           // n_groups FP64 weights
     size_t total = 0;
 };
@@ -209,8 +224,10 @@ int layout_for(const permanova_ctx* ctx, const Plan& plan_in, uint32_t n, uint64
     }
     if (form == PERMANOVA_FORM_GEMM) {
         const GemmPlan gp = gemm_plan(n, K, P, plan.gemm_ppt_div);
+        L->counter_off = off;
+        off = align_up(off + kGemmWorkCounters * sizeof(unsigned long long));
         L->gemm_off = off;
-        off = align_up(off + gemm_scratch_bytes(gp, P));
+        if (!plan.prepared) off = align_up(off + gemm_scratch_bytes(gp, P));
     }
     L->w_off = off;   // K doubles
     off = align_up(off + (size_t)K * sizeof(double));
@@ -297,12 +314,19 @@ void profile_clear(permanova_ctx* ctx) {
 // Inputs that arrive on the device while the path runs (host entry point):
 // segment k covers the 128-row bands [band[k], band[k+1]) of D and is on the
 // device once seg_ready[k] has fired; labels and weights once lab_ready has.
+// With the tensor-core form, issue_copy(k) queues segment k's copies (called
+// just before the segment's kernels are queued, so it can wait for the
+// preparation that last read its staging slot, prep_done[k - slots]), and
+// segment k sits in the band-flat layout at slot_mat[k % slots].
 struct Arrival {
     cudaEvent_t lab_ready = nullptr;
     std::vector<uint32_t> band;
     std::vector<cudaEvent_t> seg_ready;
     cudaStream_t s2 = nullptr;                 // second stream for odd segments
     cudaEvent_t fork = nullptr, join = nullptr;
+    std::function<cudaError_t(size_t)> issue_copy;
+    std::vector<const float*> slot_mat;
+    std::vector<cudaEvent_t> prep_done;
 };
 
 // The s_W path on device buffers; the arena is already large enough.
@@ -313,7 +337,7 @@ struct Arrival {
 // segment k has arrived, so the copies of later segments overlap the tensor-core
 // work on earlier ones.
 int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf, cudaStream_t s,
-           const Arrival* arr = nullptr) {
+           const Arrival* arr = nullptr, const void* prepared_ops = nullptr) {
     char* base = static_cast<char*>(ctx->arena);
     if (arr) CK(cudaStreamWaitEvent(s, arr->lab_ready, 0), "wait for labels");
     // all of D: the CUDA-core forms read every band in one launch
@@ -367,15 +391,16 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
             if (rc) return rc;
         } else {
             const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P, L.plan.gemm_ppt_div);
-            void* gs = base + L.gemm_off;
-            unsigned long long* counters = gemm_work_counters(gp, gs);
+            // the operands: prepared once for this matrix, or made now in the scratch
+            void* gs = prepared_ops ? const_cast<void*>(prepared_ops) : base + L.gemm_off;
+            unsigned long long* counters = reinterpret_cast<unsigned long long*>(base + L.counter_off);
             if (!arr) {
-                CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
+                if (!prepared_ops) CK(launch_gemm_prep(q, gp, gs, s), "GEMM operand preparation");
                 CK(cudaMemsetAsync(counters, 0, sizeof(unsigned long long), s), "reset the work counter");
                 int rc = profile_begin(ctx, s);
                 if (rc) return rc;
                 CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, s, 0, 0xFFFFFFFFu,
-                                    L.plan.gemm_drain),
+                                    L.plan.gemm_drain, counters),
                    "GEMM kernel");
                 rc = profile_end(ctx, s);
                 if (rc) return rc;
@@ -392,11 +417,20 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                 CK(cudaStreamWaitEvent(arr->s2, arr->fork, 0), "fork segment streams");
                 for (size_t k = 0; k + 1 < arr->band.size(); ++k) {
                     cudaStream_t sk = (k & 1) ? arr->s2 : s;
+                    if (arr->issue_copy) CK(arr->issue_copy(k), "copy a matrix segment");
                     CK(cudaStreamWaitEvent(sk, arr->seg_ready[k], 0), "wait for a matrix segment");
-                    CK(launch_gemm_prep(q, gp, gs, sk, arr->band[k], arr->band[k + 1]),
+                    SWProblem qk = q;   // segment k's bands, in its staging slot
+                    if (!arr->slot_mat.empty()) {
+                        qk.mat = arr->slot_mat[k % arr->slot_mat.size()];
+                        qk.banded = 1;
+                        qk.band0 = arr->band[k];
+                    }
+                    CK(launch_gemm_prep(qk, gp, gs, sk, arr->band[k], arr->band[k + 1]),
                        "GEMM operand preparation");
+                    if (!arr->prep_done.empty())
+                        CK(cudaEventRecord(arr->prep_done[k], sk), "record a segment's preparation");
                     CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, sk, arr->band[k],
-                                        arr->band[k + 1], L.plan.gemm_drain, (uint32_t)k),
+                                        arr->band[k + 1], L.plan.gemm_drain, counters + k),
                        "GEMM kernel");
                 }
                 CK(cudaEventRecord(arr->join, arr->s2), "join segment streams");
@@ -801,18 +835,36 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     SWLayout L;
     rc = layout_for(ctx, plan_for(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
     if (rc) return rc;
-    // staging for the inputs and the output after the s_W scratch.  The
-    // tensor-core form reads D only through its band trapezoids, so it stages
-    // just those (band I: rows [128 I, 128 I + 128) from column 128 I on, row
-    // stride n4 - 128 I, about half of the matrix); the CUDA-core forms get a
-    // full copy with rows of n4 floats (n4 = n rounded up to 4: 16-byte rows).
-    const bool banded = L.form == PERMANOVA_FORM_GEMM;
-    const uint64_t n4 = (n + 3ull) / 4 * 4;
-    const size_t mat_bytes = (banded ? (size_t)band_trapezoid_floats(n) : (size_t)n * n4) * sizeof(float);
+    // Staging for the inputs and the output after the s_W scratch.  Only flat
+    // copies are used: two-dimensional copies out of some page-locked host
+    // buffers ran at a fraction of the flat rate (measured: 120 against
+    // 210 GB/s from the same torch-pinned buffer).  The tensor-core form reads D
+    // only through its band trapezoids: band I is the flat host range from
+    // element (128 I, 128 I) to the end of its last row (about 128 ld floats,
+    // the rows' lower-left parts included) and lands in the band-flat layout in
+    // one of kHostSlots staging slots; the prep kernel of its segment reads it
+    // there, so the device holds kHostSlots segments of D, not all of it.  The
+    // CUDA-core forms get the whole matrix in one flat copy (row stride ld).
+    const bool gemm = L.form == PERMANOVA_FORM_GEMM;
+    const uint32_t n_bands = (n + 127) / 128;
+    const uint32_t n_seg = gemm ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
+    // segment boundaries: equal numbers of bands (the copies move about the same
+    // bytes per band)
+    std::vector<uint32_t> seg_band(n_seg + 1);
+    for (uint32_t k = 0; k <= n_seg; ++k) seg_band[k] = (uint32_t)((uint64_t)n_bands * k / n_seg);
+    auto seg_floats = [&](uint32_t k) -> uint64_t {   // floats of segment k's bands, band-flat
+        const uint32_t last = seg_band[k + 1] - 1;
+        return band_flat_offset(last, ld, n) - band_flat_offset(seg_band[k], ld, n) + band_flat_floats(last, ld, n);
+    };
+    uint64_t slot_floats = 0;
+    if (gemm)
+        for (uint32_t k = 0; k < n_seg; ++k) slot_floats = std::max(slot_floats, seg_floats(k));
+    const uint32_t n_slots = gemm ? std::min<uint32_t>(kHostSlots, n_seg) : 1u;
+    const size_t slot_bytes = align_up((gemm ? slot_floats : (uint64_t)(n - 1) * ld + n) * sizeof(float));
     const size_t lab_bytes = (size_t)n * P * label_bytes(label_type);
     size_t off = L.total;
     const size_t mat_off = off;
-    off = align_up(off + mat_bytes);
+    off = align_up(off + slot_bytes * n_slots);
     const size_t lab_off = off;
     off = align_up(off + lab_bytes);
     const size_t w_off = off;
@@ -823,21 +875,13 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     if (rc) return rc;
     char* base = static_cast<char*>(ctx->arena);
 
-    // Copies run on the context's copy stream, after the work already queued on
-    // `stream` (which may still read the arena).  Only the strict upper
-    // triangle of D is read by every form, so each 128-row band of rows
-    // [128 I, 128 I + 128) is copied from column 128 I on: about half of D.
-    // With the GEMM form the bands go in segments of equal area, each with its
-    // own event, and segment k's tensor-core work starts once it has landed.
-    const uint32_t n_bands = (n + 127) / 128;
-    const uint32_t n_seg = L.form == PERMANOVA_FORM_GEMM ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
     if (!ctx->copy_stream)
         CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "create copy stream");
     if (!ctx->seg_stream)
         CK(cudaStreamCreateWithFlags(&ctx->seg_stream, cudaStreamNonBlocking), "create segment stream");
     if (!ctx->seg_fork) CK(cudaEventCreateWithFlags(&ctx->seg_fork, cudaEventDisableTiming), "create event");
     if (!ctx->seg_join) CK(cudaEventCreateWithFlags(&ctx->seg_join, cudaEventDisableTiming), "create event");
-    while (ctx->copy_events.size() < kHostSegments + 2) {
+    while (ctx->copy_events.size() < 2 * kHostSegments + 2) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create copy event");
         ctx->copy_events.push_back(e);
@@ -869,41 +913,47 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     CK(cudaMemcpyAsync(base + w_off, w, (size_t)K * sizeof(float), cudaMemcpyHostToDevice, cs),
        "copy weights");
     CK(cudaEventRecord(arr.lab_ready, cs), "record labels");
-    // segment boundaries: equal shares of the triangle's band area
-    auto band_area = [&](uint32_t I) -> double {
-        const uint32_t r0 = 128 * I, r1 = std::min(n, r0 + 128);
-        return (double)(r1 - r0) * (double)(n - r0);
-    };
-    double total = 0.0;
-    for (uint32_t I = 0; I < n_bands; ++I) total += band_area(I);
-    arr.band.push_back(0);
-    double acc = 0.0;
     float* dmat = reinterpret_cast<float*>(base + mat_off);
-    for (uint32_t I = 0; I < n_bands; ++I) {
-        const uint32_t r0 = 128 * I, r1 = std::min(n, r0 + 128);
-        float* dst = banded ? dmat + band_trapezoid_offset(I, n4) : dmat + (uint64_t)r0 * n4 + r0;
-        const uint64_t dpitch = banded ? n4 - 128ull * I : n4;
-        CK(cudaMemcpy2DAsync(dst, dpitch * sizeof(float), mat + (uint64_t)r0 * ld + r0, ld * sizeof(float),
-                             (size_t)(n - r0) * sizeof(float), r1 - r0, cudaMemcpyHostToDevice, cs),
-           "copy matrix band");
-        if (ctx->profiling) ctx->host_h2d_bytes += (size_t)(n - r0) * sizeof(float) * (r1 - r0);
-        acc += band_area(I);
-        const size_t k = arr.band.size() - 1;   // segment being filled
-        if (I + 1 == n_bands || acc >= total * (double)(k + 1) / n_seg) {
-            cudaEvent_t e = ctx->copy_events[2 + k];
-            CK(cudaEventRecord(e, cs), "record segment");
-            if (ctx->profiling && k == 0) CK(cudaEventRecord(tev[1], cs), "record first segment");
-            arr.seg_ready.push_back(e);
-            arr.band.push_back(I + 1);
+    arr.band = seg_band;
+    for (uint32_t k = 0; k < n_seg; ++k) arr.seg_ready.push_back(ctx->copy_events[2 + k]);
+    if (gemm) {
+        for (uint32_t k = 0; k < n_slots; ++k)
+            arr.slot_mat.push_back(reinterpret_cast<const float*>(base + mat_off + (size_t)k * slot_bytes));
+        for (uint32_t k = 0; k < n_seg; ++k) arr.prep_done.push_back(ctx->copy_events[2 + kHostSegments + k]);
+        // segment k's copies, queued as its kernels are (after the preparation that
+        // last read its slot)
+        arr.issue_copy = [&, n_seg, n_slots](size_t k) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (k >= n_slots) e = cudaStreamWaitEvent(cs, arr.prep_done[k - n_slots], 0);
+            float* slot = dmat + (k % n_slots) * (slot_bytes / sizeof(float));
+            const uint64_t o0 = band_flat_offset(seg_band[k], ld, n);
+            for (uint32_t I = seg_band[k]; I < seg_band[k + 1] && e == cudaSuccess; ++I) {
+                const uint64_t r0 = 128ull * I;
+                const size_t bytes = band_flat_floats(I, ld, n) * sizeof(float);
+                e = cudaMemcpyAsync(slot + (band_flat_offset(I, ld, n) - o0), mat + r0 * ld + r0, bytes,
+                                    cudaMemcpyHostToDevice, cs);
+                if (ctx->profiling) ctx->host_h2d_bytes += bytes;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(arr.seg_ready[k], cs);
+            if (e == cudaSuccess && ctx->profiling && k == 0) e = cudaEventRecord(tev[1], cs);
+            if (e == cudaSuccess && ctx->profiling && k + 1 == n_seg) e = cudaEventRecord(tev[2], cs);
+            return e;
+        };
+    } else {
+        const size_t bytes = ((uint64_t)(n - 1) * ld + n) * sizeof(float);
+        CK(cudaMemcpyAsync(dmat, mat, bytes, cudaMemcpyHostToDevice, cs), "copy matrix");
+        if (ctx->profiling) ctx->host_h2d_bytes += bytes;
+        CK(cudaEventRecord(arr.seg_ready[0], cs), "record matrix");
+        if (ctx->profiling) {
+            CK(cudaEventRecord(tev[1], cs), "record first segment");
+            CK(cudaEventRecord(tev[2], cs), "record last segment");
         }
     }
-    if (ctx->profiling) CK(cudaEventRecord(tev[2], cs), "record last segment");
     // the staged label buffer is 256-byte aligned: re-plan so the direct path can be taken
-    rc = layout_for(ctx, L.plan, n, n4, base + lab_off, label_type, K, P, &L);
+    rc = layout_for(ctx, L.plan, n, ld, base + lab_off, label_type, K, P, &L);
     if (rc) return rc;
-    SWProblem pr{reinterpret_cast<const float*>(dmat), n, n4, base + lab_off, label_type, K,
+    SWProblem pr{reinterpret_cast<const float*>(dmat), n, ld, base + lab_off, label_type, K,
                  P, nullptr, reinterpret_cast<double*>(base + out_off)};
-    pr.banded = banded ? 1u : 0u;
     rc = run_sW(ctx, L, pr, reinterpret_cast<const float*>(base + w_off), s, &arr);
     if (rc) return rc;
     CK(cudaMemcpyAsync(out, base + out_off, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -946,10 +996,13 @@ int permanova_test_batch(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
                                 out_sW, stream);
 }
 
-int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
-                         const int32_t* groupings, uint32_t T, const uint32_t* Ks, const uint64_t* Ps,
-                         const uint64_t* seeds, permanova_result* out_host, double* out_sW,
-                         void* stream) {
+}  // extern "C"
+
+namespace {
+// permanova_test_mixed, with the tensor-core operands optionally prepared
+int test_mixed_impl(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, const void* prepared_ops,
+                    const int32_t* groupings, uint32_t T, const uint32_t* Ks, const uint64_t* Ps,
+                    const uint64_t* seeds, permanova_result* out_host, double* out_sW, void* stream) {
     if (!ctx) return fail(PERMANOVA_EINVAL, "ctx is NULL");
     if (!mat || !groupings || !out_host || !seeds || !Ks || !Ps)
         return fail(PERMANOVA_EINVAL, "NULL pointer argument");
@@ -1029,6 +1082,7 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
         uint32_t Kg = 0;
         while (e < T && pid[order[e]] == pid[order[k]]) Kg = std::max(Kg, ks[e++]);
         FormGroup fg{k, e, Kg, plans[pid[order[k]]], gw.size(), grs.size()};
+        if (prepared_ops && fg.plan.form == PERMANOVA_FORM_GEMM) fg.plan.prepared = true;
         for (uint32_t q = k; q < e; ++q)
             for (uint32_t c = 0; c < Kg; ++c) gw.push_back(hw[(size_t)order[q] * Kmax + c]);
         for (uint32_t q = k; q <= e; ++q) grs.push_back(rs[q] - rs[k]);
@@ -1099,7 +1153,7 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
         SWProblem pr{mat, n, ld, glab, lt, fg.K, nr, dw + fg.w_off, sW + r0};
         pr.w_row_start = dgrs + fg.rs_off;
         pr.w_sets = fg.t1 - fg.t0;
-        rc = run_sW(ctx, L, pr, nullptr, s);
+        rc = run_sW(ctx, L, pr, nullptr, s, nullptr, fg.plan.prepared ? prepared_ops : nullptr);
         if (rc) return rc;
     }
     CK(launch_sumsq_triangle(mat, n, ld, chunks, st_part, s), "sum of squares kernel");
@@ -1131,6 +1185,89 @@ int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint6
         out_host[t].n_perms = hres[k].n_perms;
     }
     return PERMANOVA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int permanova_test_mixed(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
+                         const int32_t* groupings, uint32_t T, const uint32_t* Ks, const uint64_t* Ps,
+                         const uint64_t* seeds, permanova_result* out_host, double* out_sW,
+                         void* stream) {
+    return test_mixed_impl(ctx, mat, n, ld, nullptr, groupings, T, Ks, Ps, seeds, out_host, out_sW, stream);
+}
+
+int permanova_prepare(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld, permanova_prepared** out,
+                      void* stream) {
+    if (!ctx || !out) return fail(PERMANOVA_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (!mat) return fail(PERMANOVA_EINVAL, "mat is NULL");
+    if (n < 2) return fail(PERMANOVA_EINVAL, "n_dims must be >= 2 (got %u)", n);
+    if (ld < n) return fail(PERMANOVA_EINVAL, "ld (%llu) < n_dims (%u)", (unsigned long long)ld, n);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GemmPlan gp = gemm_plan(n, 1, 1);   // the operands depend on n alone
+    auto* p = new permanova_prepared();
+    p->device = ctx->device;
+    p->mat = mat;
+    p->n = n;
+    p->ld = ld;
+    p->bytes = gemm_scratch_bytes(gp, 0);
+    cudaError_t e = cudaMalloc(&p->ops, p->bytes);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaMalloc(prepared operands)");
+    }
+    SWProblem pr{mat, n, ld, nullptr, LABEL_U8, 1, 1, nullptr, nullptr};
+    e = launch_gemm_prep(pr, gp, p->ops, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(p->ops);
+        delete p;
+        return cuda_fail(e, "operand preparation");
+    }
+    *out = p;
+    return PERMANOVA_OK;
+}
+
+void permanova_prepared_destroy(permanova_prepared* p) {
+    if (!p) return;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        if (p->ops) cudaFree(p->ops);
+    }
+    delete p;
+}
+
+int permanova_sW_prepared(permanova_ctx* ctx, const permanova_prepared* prep, const void* groupings,
+                          int label_type, uint32_t K, uint64_t P, const float* w, double* out, void* stream) {
+    if (!ctx || !prep) return fail(PERMANOVA_EINVAL, "NULL argument");
+    if (prep->device != ctx->device) return fail(PERMANOVA_EINVAL, "prepared on another device");
+    int rc = check_sW_args(prep->mat, prep->n, prep->ld, groupings, label_type, K, P, w, out);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan pl = plan_for(ctx, prep->n, K, P);
+    if (pl.form == PERMANOVA_FORM_GEMM) pl.prepared = true;
+    SWLayout L;
+    rc = layout_for(ctx, pl, prep->n, prep->ld, groupings, label_type, K, P, &L);
+    if (rc) return rc;
+    rc = ensure_arena(ctx, L.total);
+    if (rc) return rc;
+    SWProblem pr{prep->mat, prep->n, prep->ld, groupings, label_type, K, P, nullptr, out};
+    return run_sW(ctx, L, pr, w, s, nullptr, pl.prepared ? prep->ops : nullptr);
+}
+
+int permanova_test_mixed_prepared(permanova_ctx* ctx, const permanova_prepared* prep, const int32_t* groupings,
+                                  uint32_t T, const uint32_t* Ks, const uint64_t* Ps, const uint64_t* seeds,
+                                  permanova_result* out_host, double* out_sW, void* stream) {
+    if (!ctx || !prep) return fail(PERMANOVA_EINVAL, "NULL argument");
+    if (prep->device != ctx->device) return fail(PERMANOVA_EINVAL, "prepared on another device");
+    return test_mixed_impl(ctx, prep->mat, prep->n, prep->ld, prep->ops, groupings, T, Ks, Ps, seeds, out_host,
+                           out_sW, stream);
 }
 
 }  // extern "C"

@@ -27,6 +27,10 @@ launch and of the padded group count, the kernel form chosen by a single
 test's sizes), so a test gives bit-identical s_W, F and p alone, batched and
 among other traffic.
 
+With ``prepare=True`` each resident matrix's tensor-core operands are made
+once, on its first request, and shared by every slot (about 2 n^2 bytes per
+matrix), so later requests skip that pass over the matrix.
+
 Latency is measured from arrival (submit) to completion; the server reports
 tests/s and p50/p99 latency.  With ``max_pending`` set, a request that finds
 that many requests already waiting is refused at once ("server busy"), so
@@ -120,7 +124,7 @@ class Server:
 
     def __init__(self, matrices: dict, n_slots: int = 4, hbm_budget_bytes: int = 0,
                  device: int = 0, max_batch: int = 16, reserve_per_slot: int = 0,
-                 max_pending: int = 0):
+                 max_pending: int = 0, prepare: bool = False):
         import torch
         self.torch = torch
         self.max_batch = max_batch
@@ -145,6 +149,11 @@ class Server:
             for k, (ctx, _) in enumerate(self.slots):
                 pm.permanova_reserve_scratch(ctx.handle, per)
                 self.reserved[k] = pm.permanova_scratch_reserved(ctx.handle)
+        # prepared matrices: the tensor-core operands of each resident matrix made
+        # once (on its first request) and shared by every slot
+        self.prepare = prepare
+        self.prepared: dict = {}
+        self.prep_lock = threading.Lock()
         self.charged = [0] * n_slots      # bytes charged to the batch running on a slot
         self.busy = [False] * n_slots
         self.completed: list[Request] = []
@@ -228,11 +237,14 @@ class Server:
             with torch.cuda.stream(stream):
                 g = torch.from_numpy(np.stack([r.grouping for r in batch]).astype(np.int32)).to(
                     device=D.device, non_blocking=False)
-                results = pm.permanova_test_mixed(ctx.handle, D, D.shape[0], D.stride(0), g,
-                                                  [r.n_groups for r in batch],
-                                                  [r.n_perms for r in batch],
-                                                  [r.seed for r in batch],
-                                                  stream=stream.cuda_stream)
+                args = ([r.n_groups for r in batch], [r.n_perms for r in batch], [r.seed for r in batch])
+                prep = self._prepared(head.matrix_id, ctx, stream) if self.prepare else None
+                if prep is not None:
+                    results = pm.permanova_test_mixed_prepared(ctx.handle, prep, g, *args,
+                                                               stream=stream.cuda_stream)
+                else:
+                    results = pm.permanova_test_mixed(ctx.handle, D, D.shape[0], D.stride(0), g, *args,
+                                                      stream=stream.cuda_stream)
             for r, res in zip(batch, results):
                 r.result = res
         except Exception as e:  # reported per request; the server keeps running
@@ -254,11 +266,25 @@ class Server:
             for r in batch:
                 r.done.set()
 
+    def _prepared(self, matrix_id: int, ctx, stream):
+        """The prepared operands of a resident matrix, made on first use."""
+        with self.prep_lock:
+            prep = self.prepared.get(matrix_id)
+            if prep is None:
+                D = self.matrices[matrix_id]
+                prep = pm.permanova_prepare(ctx.handle, D, D.shape[0], D.stride(0),
+                                            stream=stream.cuda_stream)
+                self.prepared[matrix_id] = prep
+            return prep
+
     def close(self):
         with self.cv:
             self.running = False
             self.cv.notify_all()
         self.dispatcher.join(timeout=5)
+        for prep in self.prepared.values():
+            pm.permanova_prepared_destroy(prep)
+        self.prepared.clear()
         for ctx, _ in self.slots:
             ctx.close()
 

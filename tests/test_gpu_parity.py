@@ -375,12 +375,13 @@ def test_host_entry_point(ctx):
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,ld", [(1000, 1003), (2177, 2177)])
 def test_host_entry_segments(ctx, form, n, ld):
-    """The host entry point copies only the band trapezoids of D (the lower
-    triangle below them never reaches the device) and, with the tensor-core
-    form, runs band segments as they land: results equal the device entry
-    point's bit for bit (on a device copy with the staged row stride, n
-    rounded up to 4 floats: the brute-force kernel's summation order depends
-    on whether rows are 16-byte aligned) and the oracle's within tolerance."""
+    """The host entry point copies D with flat copies (each band's host range
+    with the tensor-core form, which runs band segments as they land through
+    three staging slots; the whole matrix otherwise) and never reads the
+    lower triangle: results equal the device entry point's bit for bit (on a
+    device copy with the caller's row stride: the brute-force kernel's
+    summation order depends on whether rows are 16-byte aligned) and the
+    oracle's within tolerance."""
     K, P = 5, 70
     D, rows, w = _case(n, K, P, seed=37)
     Dp = np.full((n, ld), np.nan, dtype=np.float32)
@@ -394,7 +395,7 @@ def test_host_entry_segments(ctx, form, n, ld):
                              np.ascontiguousarray(w, dtype=np.float32), out)
     finally:
         ctx.set_form(pm.FORM_AUTO)
-    dev = _run_sW(ctx, D, rows, K, w, form, pm.LABEL_U8, ld=(n + 3) // 4 * 4)
+    dev = _run_sW(ctx, D, rows, K, w, form, pm.LABEL_U8, ld=ld)
     np.testing.assert_array_equal(out, dev)
     idx = np.arange(0, P, 7)
     ref = oracle.sW_alg1(D, rows[idx], K, w.astype(np.float64))
@@ -403,7 +404,7 @@ def test_host_entry_segments(ctx, form, n, ld):
 
 def test_host_entry_profile(ctx):
     """With profiling on, the host entry point records one call, the bytes it
-    copied (the band trapezoids of D, the labels and the weights) and an
+    copied (each band's flat host range, the labels and the weights) and an
     ordered device timeline: first segment <= last segment <= end."""
     n, ld, K, P = 1000, 1003, 5, 70
     D, rows, w = _case(n, K, P, seed=41)
@@ -420,9 +421,10 @@ def test_host_entry_profile(ctx):
     finally:
         pm.permanova_profile_enable(ctx.handle, False)
         ctx.set_form(pm.FORM_AUTO)
-    trap = sum(min(128, n - r0) * (n - r0) * 4 for r0 in range(0, n, 128))
+    # each band's flat host range: from (128 I, 128 I) to the end of its last row
+    bands = sum(((min(128, n - r0) - 1) * ld + n - r0) * 4 for r0 in range(0, n, 128))
     assert prof["host_calls"] == 1
-    assert prof["host_h2d_bytes"] == trap + n * P + 4 * K
+    assert prof["host_h2d_bytes"] == bands + n * P + 4 * K
     assert 0.0 < prof["host_first_segment_ms"] <= prof["host_copy_ms"] <= prof["host_total_ms"]
     ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
     np.testing.assert_allclose(out, ref, rtol=RTOL)

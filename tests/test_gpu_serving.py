@@ -238,3 +238,25 @@ def test_back_pressure_refuses_beyond_the_waiting_limit(matrices):
     busy = [r for r in reqs if r.error and "server busy" in r.error]
     served = [r for r in reqs if r.error is None]
     assert busy and served and len(busy) + len(served) == len(reqs)
+
+
+def test_prepared_server_results_equal_unprepared(matrices):
+    """A server that prepares its matrices gives the results of one that
+    does not, request for request."""
+    from paper_2505_04556_gb300.serve import Server
+    mats, hosts = matrices
+    out = []
+    for prepare in (False, True):
+        srv = Server(mats, n_slots=2, prepare=prepare)
+        try:
+            reqs = _requests(hosts, 9)
+            for r in reqs:
+                srv.submit(r)
+            for r in reqs:
+                assert r.done.wait(120) and r.error is None, r.error
+            if prepare:
+                assert srv.prepared
+        finally:
+            srv.close()
+        out.append([r.result for r in reqs])
+    assert out[0] == out[1]

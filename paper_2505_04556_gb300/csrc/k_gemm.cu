@@ -34,9 +34,10 @@
 // then one per band that of its smallest nonzero d^2.
 //
 // Kernel.  Persistent, one CTA per SM, 16 warps:
-//   warp 0       bulk-copies the A tiles into a 4-stage ring and the 64-column
-//                label slices of the tile's label rows into a label ring that
-//                runs up to 16 k-blocks ahead;
+//   warp 0       takes work units from the launch's work counter and publishes
+//                them in a unit ring; bulk-copies the A tiles into a 4-stage
+//                ring and the 64-column label slices of the tile's label rows
+//                into a label ring that runs up to 16 k-blocks ahead;
 //   warp 1       owns 512 TMEM columns (two 128 x 256 FP32 accumulators) and
 //                issues the tcgen05.mma instructions (one thread);
 //   warps 4-7    drain the accumulators (tcgen05.ld, four rows of a column per
@@ -46,8 +47,10 @@
 //                B row per thread; for even K, two B rows of a label row per
 //                thread (one label read and byte permute for both), warps 8-11
 //                building stage 0 and warps 12-15 stage 1.
-// Work unit = (band I, tile of up to 128 label rows), band-major so the CTAs
-// running together share a band and read its A tiles from L2.
+// Work unit = (band I, tile of up to 128 label rows), numbered band-major and
+// handed out in that order by the work counter, so the CTAs running together
+// share a band and read its A tiles from L2, and a CTA that finishes early
+// takes more units.
 // Every wait is bounded; on timeout the kernel records DEV_TIMEOUT, lets the
 // other roles run out, waits for its own copies and MMAs, frees its TMEM and
 // returns.
@@ -843,7 +846,6 @@ __global__ void __launch_bounds__(g::THREADS, 1) k_gemm_main(GemmArgs a) {
         // per unit, and the four warps' sums are added in a fixed order.
         const uint32_t et = threadIdx.x - 128;     // 0..127
         const uint32_t q4 = warp - 4;              // TMEM lane quarter
-        const uint32_t row = q4 * 32 + lane;       // row within the band
         const uint32_t K = a.K;
         const uint32_t used = a.ppt * K;           // accumulator columns that carry a (p, g)
         uint64_t cc = 0;

@@ -1,5 +1,9 @@
 // Perm-blocked CUDA-core s_W: one 64 x 64 tile of D^2 in shared memory is
-// reused by a block of 128 label rows, one label row per thread.
+// reused by a block of label rows.  Two kernels: the paired kernel below the
+// first (uint8 codes, the default: 256 label rows per block, two per thread,
+// one packed FP16 compare per two evaluations) and this one (128 label rows
+// per block, one per thread, FP32 compare-and-set; uint16 codes and plan
+// variant 1).
 //
 // Algorithm 1 evaluates, per label row p and pair i < j, the test
 // g_p(i) == g_p(j) and adds d_ij^2 * w_{g_p(i)} (Sec. 2).  Here a CTA owns a

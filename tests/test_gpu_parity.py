@@ -274,6 +274,19 @@ def test_permutations_bit_exact_with_oracle(ctx):
         assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("n", [2, 3, 7, 8, 9, 16, 17, 1000, 5003])
+def test_permutations_bit_exact_across_row_lengths(ctx, n):
+    """Row lengths below, at and around the shuffle's prefetch window (8 steps)
+    and long rows: every row equals the oracle's Fisher-Yates shuffle."""
+    K = 2 if n < 8 else 5
+    obs = synth.observed_labels([n // K] * (K - 1) + [n - (K - 1) * (n // K)], 7)
+    for ltype, tdt in ((pm.LABEL_U8, torch.uint8), (pm.LABEL_I32, torch.int32)):
+        out = torch.empty((41, n), dtype=tdt, device="cuda")
+        pm.permanova_permutations(ctx.handle, _dev(obs), n, K, 40, 77 + n, out, ltype)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.permutations(obs, 40, 77 + n))
+
+
 @pytest.mark.parametrize("n,K,P,seed", [(60, 2, 99, 1), (257, 3, 999, 2), (1000, 3, 999, 3)])
 def test_permanova_test_matches_oracle(ctx, n, K, P, seed):
     cfg = synth.recipe("euclid-1k", n=n, P=P)

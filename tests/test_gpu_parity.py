@@ -274,10 +274,13 @@ def test_permutations_bit_exact_with_oracle(ctx):
         assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("n", [2, 3, 7, 8, 9, 16, 17, 1000, 5003])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 9, 16, 17, 1000, 5003, 50000, 60000])
 def test_permutations_bit_exact_across_row_lengths(ctx, n):
-    """Row lengths below, at and around the shuffle's prefetch window (8 steps)
-    and long rows: every row equals the oracle's Fisher-Yates shuffle."""
+    """Short and long rows, shuffled in shared memory (rows that fit four or
+    more to a block) or in place in HBM (n = 60,000: three uint8 rows or no
+    int32 row fit): every row equals the oracle's Fisher-Yates shuffle.  At
+    n >= 50,000 some draws need Lemire's rejection check (about 0.3 draws per
+    row at 50,000, 0.4 at 60,000), which the shuffle takes one at a time."""
     K = 2 if n < 8 else 5
     obs = synth.observed_labels([n // K] * (K - 1) + [n - (K - 1) * (n // K)], 7)
     for ltype, tdt in ((pm.LABEL_U8, torch.uint8), (pm.LABEL_I32, torch.int32)):

@@ -848,10 +848,20 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     const bool gemm = L.form == PERMANOVA_FORM_GEMM;
     const uint32_t n_bands = (n + 127) / 128;
     const uint32_t n_seg = gemm ? std::min<uint32_t>(kHostSegments, n_bands) : 1u;
-    // segment boundaries: equal numbers of bands (the copies move about the same
-    // bytes per band)
-    std::vector<uint32_t> seg_band(n_seg + 1);
-    for (uint32_t k = 0; k <= n_seg; ++k) seg_band[k] = (uint32_t)((uint64_t)n_bands * k / n_seg);
+    // segment boundaries: the first segments small (band counts in the ratio
+    // 1 : 2 : 4 : 8 : 8 : ...), so the kernels start after a short copy and each
+    // early segment's kernels cover the next one's copy; the copies move about
+    // the same bytes per band
+    std::vector<uint32_t> seg_band(n_seg + 1, 0);
+    {
+        std::vector<uint64_t> cum(n_seg + 1, 0);
+        for (uint32_t k = 0; k < n_seg; ++k) cum[k + 1] = cum[k] + (k < 3 ? (1ull << k) : 8ull);
+        for (uint32_t k = 1; k <= n_seg; ++k) {
+            uint32_t b = (uint32_t)((n_bands * cum[k] + cum[n_seg] / 2) / cum[n_seg]);
+            b = std::max(b, seg_band[k - 1] + 1);                // every segment has a band
+            seg_band[k] = std::min(b, n_bands - (n_seg - k));    // and leaves one for each after it
+        }
+    }
     auto seg_floats = [&](uint32_t k) -> uint64_t {   // floats of segment k's bands, band-flat
         const uint32_t last = seg_band[k + 1] - 1;
         return band_flat_offset(last, ld, n) - band_flat_offset(seg_band[k], ld, n) + band_flat_floats(last, ld, n);

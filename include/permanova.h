@@ -215,9 +215,11 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
  * s_W, copies the n_perms results back and synchronises `stream`.  All copies
  * are flat (one-dimensional).  With the tensor-core form each 128-row band b
  * is copied as the host range from element (128 b, 128 b) to the end of the
- * band's last row, in up to 16 segments through three device staging slots
- * of about a sixteenth of the matrix each, and each segment's kernels start
- * as soon as it has landed, so the copies overlap the computation; segments
+ * band's last row, in up to 16 segments (band counts ramping up 1 : 2 : 4 :
+ * 8 : 8 : ..., so the kernels start after a short first copy) through three
+ * device staging slots sized for the largest segment, and each segment's
+ * kernels start as soon as it has landed, so the copies overlap the
+ * computation; segments
  * alternate between `stream` and a second stream of the context (joined back
  * into `stream` before the final reduction), so one segment's last wave of
  * blocks overlaps the next segment's first.  The CUDA-core forms copy the

@@ -690,7 +690,9 @@ def main():
                     "last_segment_landed_ms": round(hp["host_copy_ms"] / calls, 2),
                     "h2d_gbs_in_step": round(hp["host_h2d_bytes"] / max(1e-9, hp["host_copy_ms"] / 1e3)
                                              / 1e9, 1),
-                    "kernel_ms_device_resident": round(kernel_ms * B / (rows_done / launches), 2)}
+                    "kernel_ms_device_resident": round(kernel_ms * B / (rows_done / launches), 2),
+                    "segments_landed_ms": [round(x / calls, 1) for x in hp["host_seg_landed_ms"]],
+                    "segments_kernel_done_ms": [round(x / calls, 1) for x in hp["host_seg_done_ms"]]}
         e2e = {"value": pairs * rows_e2e / te, "unit": UNIT,
                "h2d_bytes_per_step": int(host_matrix_bytes(n, n) + B * n + K * 4),
                "d2h_bytes_per_step": int(B * 8), "steps": args.e2e_steps, "step_ms": step_ms,

@@ -283,9 +283,9 @@ int permanova_permutations(permanova_ctx *ctx, const int32_t *grouping, uint32_t
  * support).  While enabled, every s_W call on device buffers records CUDA
  * events on its stream around its dominant kernel (the brute-force, perm-block
  * or GEMM kernel), every kernel the library launches is counted, and every
- * permanova_sW_host call records events at its start, when the first and the
- * last segment of the matrix have landed on the device, and at its end (the
- * results copied back). */
+ * permanova_sW_host call records events at its start, when each segment of
+ * the matrix has landed on the device, when each segment's dominant kernel
+ * has run, and at its end (the results copied back). */
 typedef struct {
     double main_kernel_ms;          /* summed event time of the dominant kernels */
     uint64_t main_kernel_launches;  /* dominant-kernel launches recorded */
@@ -296,6 +296,12 @@ typedef struct {
     double host_first_segment_ms;   /* summed time until the first matrix segment landed */
     double host_copy_ms;            /* summed time until the last matrix segment landed */
     uint64_t host_h2d_bytes;        /* bytes those calls copied host to device */
+    uint32_t host_segments;         /* matrix segments of the last recorded call (<= 16;
+                                       1 for the CUDA-core forms, which copy D whole) */
+    double host_seg_landed_ms[16];  /* per segment k: summed time, call start to segment
+                                       k landed (calls with fewer segments add nothing) */
+    double host_seg_done_ms[16];    /* per segment k: summed time, call start to segment
+                                       k's dominant kernel done */
 } permanova_profile_t;
 
 /* Enable (1) or disable (0) profiling; enabling clears the counters. */

@@ -57,10 +57,15 @@ class permanova_profile_t(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("last_form", ctypes.c_int),
                 ("host_calls", ctypes.c_uint64), ("host_total_ms", ctypes.c_double),
                 ("host_first_segment_ms", ctypes.c_double), ("host_copy_ms", ctypes.c_double),
-                ("host_h2d_bytes", ctypes.c_uint64)]
+                ("host_h2d_bytes", ctypes.c_uint64), ("host_segments", ctypes.c_uint32),
+                ("host_seg_landed_ms", ctypes.c_double * 16), ("host_seg_done_ms", ctypes.c_double * 16)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        m = min(16, d["host_segments"])
+        d["host_seg_landed_ms"] = list(d["host_seg_landed_ms"])[:m]
+        d["host_seg_done_ms"] = list(d["host_seg_done_ms"])[:m]
+        return d
 
 
 _lock = threading.Lock()

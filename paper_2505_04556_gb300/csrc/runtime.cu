@@ -73,6 +73,9 @@ struct permanova_ctx {
     // host entry point (profiling): per call, timing events at its start, when
     // the first and the last matrix segment have landed, and at its end
     std::vector<std::array<cudaEvent_t, 4>> host_events;
+    // per host-entry call (same index as host_events): segment k landed for
+    // k < m, then segment k's dominant kernel done, m segments
+    std::vector<std::vector<cudaEvent_t>> host_seg_events;
     uint64_t host_h2d_bytes = 0;
     // host entry point: copies run on their own stream, ordered by events;
     // matrix segments alternate between the caller's stream and seg_stream so
@@ -307,6 +310,9 @@ void profile_clear(permanova_ctx* ctx) {
     for (auto& h : ctx->host_events)
         for (cudaEvent_t e : h) cudaEventDestroy(e);
     ctx->host_events.clear();
+    for (auto& v : ctx->host_seg_events)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    ctx->host_seg_events.clear();
     ctx->host_h2d_bytes = 0;
     ctx->launch_mark = kernel_launch_count();
 }
@@ -327,6 +333,9 @@ struct Arrival {
     std::function<cudaError_t(size_t)> issue_copy;
     std::vector<const float*> slot_mat;
     std::vector<cudaEvent_t> prep_done;
+    // timing events (profiling only, else empty): segment k landed, and its
+    // dominant kernel done
+    std::vector<cudaEvent_t> t_landed, t_done;
 };
 
 // The s_W path on device buffers; the arena is already large enough.
@@ -362,6 +371,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
         CK(launch_brute(pr, L.part_rows, partials, ctx->status, s), "brute-force kernel");
         rc = profile_end(ctx, s);
         if (rc) return rc;
+        if (arr && !arr->t_done.empty()) CK(cudaEventRecord(arr->t_done[0], s), "record kernel done");
     } else {
         if (L.repack) {
             void* codes = base + L.lab_off;
@@ -389,6 +399,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                "perm-block kernel");
             rc = profile_end(ctx, s);
             if (rc) return rc;
+            if (arr && !arr->t_done.empty()) CK(cudaEventRecord(arr->t_done[0], s), "record kernel done");
         } else {
             const GemmPlan gp = gemm_plan(pr.n, pr.K, pr.P, L.plan.gemm_ppt_div);
             // the operands: prepared once for this matrix, or made now in the scratch
@@ -432,6 +443,7 @@ int run_sW(permanova_ctx* ctx, const SWLayout& L, SWProblem pr, const float* wf,
                     CK(launch_gemm_main(q, gp, gs, partials, ctx->status, ctx->sm_count, sk, arr->band[k],
                                         arr->band[k + 1], L.plan.gemm_drain, counters + k),
                        "GEMM kernel");
+                    if (!arr->t_done.empty()) CK(cudaEventRecord(arr->t_done[k], sk), "record kernel done");
                 }
                 CK(cudaEventRecord(arr->join, arr->s2), "join segment streams");
                 CK(cudaStreamWaitEvent(s, arr->join, 0), "join segment streams");
@@ -809,6 +821,20 @@ int permanova_profile_read(permanova_ctx* ctx, permanova_profile_t* out) {
         out->host_copy_ms += b;
         out->host_total_ms += c;
     }
+    out->host_segments = 0;
+    for (int k = 0; k < 16; ++k) out->host_seg_landed_ms[k] = out->host_seg_done_ms[k] = 0.0;
+    for (size_t c = 0; c < ctx->host_seg_events.size() && c < ctx->host_events.size(); ++c) {
+        const auto& v = ctx->host_seg_events[c];
+        const size_t m = v.size() / 2;
+        out->host_segments = (uint32_t)m;
+        for (size_t k = 0; k < m && k < 16; ++k) {
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, ctx->host_events[c][0], v[k]), "cudaEventElapsedTime");
+            CK(cudaEventElapsedTime(&b, ctx->host_events[c][0], v[m + k]), "cudaEventElapsedTime");
+            out->host_seg_landed_ms[k] += a;
+            out->host_seg_done_ms[k] += b;
+        }
+    }
     out->host_h2d_bytes = ctx->host_h2d_bytes;
     out->kernel_launches = kernel_launch_count() - ctx->launch_mark;
     out->last_form = ctx->last_form;
@@ -896,7 +922,8 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create copy event");
         ctx->copy_events.push_back(e);
     }
-    // profiling: timing events at the start, first segment, last segment, end
+    // profiling: timing events at the start, first segment, last segment and end,
+    // and per segment when it landed and when its dominant kernel had run
     std::array<cudaEvent_t, 4> tev{};
     if (ctx->profiling) {
         for (auto& e : tev) {
@@ -907,6 +934,16 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
             }
         }
         ctx->host_events.push_back(tev);
+        std::vector<cudaEvent_t> sev(2 * (size_t)n_seg, nullptr);
+        for (auto& e : sev) {
+            if (cudaError_t ce = cudaEventCreate(&e); ce != cudaSuccess) {
+                for (cudaEvent_t x : sev)
+                    if (x) cudaEventDestroy(x);
+                ctx->host_seg_events.emplace_back();   // keeps the two lists aligned
+                return cuda_fail(ce, "cudaEventCreate");
+            }
+        }
+        ctx->host_seg_events.push_back(sev);
         ctx->host_h2d_bytes += lab_bytes + (size_t)K * sizeof(float);
         CK(cudaEventRecord(tev[0], s), "record start");
     }
@@ -926,6 +963,11 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     float* dmat = reinterpret_cast<float*>(base + mat_off);
     arr.band = seg_band;
     for (uint32_t k = 0; k < n_seg; ++k) arr.seg_ready.push_back(ctx->copy_events[2 + k]);
+    if (ctx->profiling) {
+        const auto& sev = ctx->host_seg_events.back();
+        arr.t_landed.assign(sev.begin(), sev.begin() + n_seg);
+        arr.t_done.assign(sev.begin() + n_seg, sev.end());
+    }
     if (gemm) {
         for (uint32_t k = 0; k < n_slots; ++k)
             arr.slot_mat.push_back(reinterpret_cast<const float*>(base + mat_off + (size_t)k * slot_bytes));
@@ -945,6 +987,7 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
                 if (ctx->profiling) ctx->host_h2d_bytes += bytes;
             }
             if (e == cudaSuccess) e = cudaEventRecord(arr.seg_ready[k], cs);
+            if (e == cudaSuccess && !arr.t_landed.empty()) e = cudaEventRecord(arr.t_landed[k], cs);
             if (e == cudaSuccess && ctx->profiling && k == 0) e = cudaEventRecord(tev[1], cs);
             if (e == cudaSuccess && ctx->profiling && k + 1 == n_seg) e = cudaEventRecord(tev[2], cs);
             return e;
@@ -955,6 +998,7 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
         if (ctx->profiling) ctx->host_h2d_bytes += bytes;
         CK(cudaEventRecord(arr.seg_ready[0], cs), "record matrix");
         if (ctx->profiling) {
+            CK(cudaEventRecord(arr.t_landed[0], cs), "record segment landed");
             CK(cudaEventRecord(tev[1], cs), "record first segment");
             CK(cudaEventRecord(tev[2], cs), "record last segment");
         }

@@ -421,7 +421,8 @@ def test_host_entry_segments(ctx, form, n, ld):
 def test_host_entry_profile(ctx):
     """With profiling on, the host entry point records one call, the bytes it
     copied (each band's flat host range, the labels and the weights) and an
-    ordered device timeline: first segment <= last segment <= end."""
+    ordered device timeline: first segment <= last segment <= end, and per
+    segment the time it landed and the time its kernel had run."""
     n, ld, K, P = 1000, 1003, 5, 70
     D, rows, w = _case(n, K, P, seed=41)
     Dp = np.zeros((n, ld), dtype=np.float32)
@@ -442,5 +443,12 @@ def test_host_entry_profile(ctx):
     assert prof["host_calls"] == 1
     assert prof["host_h2d_bytes"] == bands + n * P + 4 * K
     assert 0.0 < prof["host_first_segment_ms"] <= prof["host_copy_ms"] <= prof["host_total_ms"]
+    # per segment (8 bands, one segment each): landed in copy order, each
+    # segment's kernel after its copy and before the end of the call
+    landed, done = prof["host_seg_landed_ms"], prof["host_seg_done_ms"]
+    assert prof["host_segments"] == len(landed) == len(done) == 8
+    assert landed == sorted(landed)
+    assert all(0.0 < a <= b <= prof["host_total_ms"] for a, b in zip(landed, done))
+    assert landed[0] <= prof["host_first_segment_ms"] and landed[-1] <= prof["host_copy_ms"]
     ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
     np.testing.assert_allclose(out, ref, rtol=RTOL)

@@ -3,6 +3,7 @@
 // test (Sec. 1) and the test's final statistics.
 #include "common.cuh"
 
+#include <algorithm>
 #include <atomic>
 
 namespace pmn {
@@ -206,16 +207,18 @@ struct Philox4x32 {
 // Shuffles.  Every permutation row is a Fisher-Yates shuffle of its test's
 // observed labels: for i = n-1 down to 1, swap a[i] with a[j], j drawn
 // uniformly from [0, i] by the row's Philox stream (seed of the test, counter
-// (block, 0, p, 0) for row p).  One thread per row: a step depends on the
-// previous one, so a row takes n steps of memory latency, and where the row
-// lives decides that latency.
+// (block, 0, p, 0) for row p).  A step depends on the previous one, so a row
+// takes n dependent steps; where the row lives and what sits on a step's
+// chain decide their latency (fy_plan picks the path).
 //
-// Staged path (rows that fit, 4 or more to a block): a block copies the
-// observed labels of up to 128 rows into shared memory, each thread shuffles
-// its row there (a step is a few shared-memory accesses), and the block
-// writes the rows back coalesced.  Global path (longer rows): each thread
-// shuffles its row in place in HBM (the rows copied there first); every step
-// then waits on an L2 or DRAM round trip.
+// Staged path (short rows, many to a block): a block copies the observed
+// labels of up to 128 rows into shared memory, each thread shuffles its row
+// there (a step is a few shared-memory accesses), and the block writes the
+// rows back coalesced.  Warp path (long rows, or few): the same with a warp
+// per row, its lanes preparing the draws and swap targets (k_shuffle_warp).
+// Global path (rows too long for shared memory): each thread shuffles its row
+// in place in HBM (the rows copied there first); every step then waits on an
+// L2 or DRAM round trip.
 //
 // Rows of a batch map to (test, p) by the tests' row starts: test t owns rows
 // [rs[t], rs[t+1]) of the output, the first its observed grouping (row src[t]
@@ -262,6 +265,38 @@ __device__ __forceinline__ void philox_block(uint32_t k0, uint32_t k1, uint32_t 
     r.block(x);
 }
 
+// Four Fisher-Yates steps i, i-1, i-2, i-3 with targets J[0..3] (J[t] <= i-t).
+// When no target falls among the four positions and the targets differ, the
+// four swaps touch disjoint positions, so all eight loads go out before the
+// eight stores (one memory round trip instead of four); otherwise the swaps
+// run one after the other.  Either way the result is that of the sequence.
+template <typename L>
+__device__ __forceinline__ void swap4(L* a, uint32_t i, const uint32_t (&J)[4]) {
+    const uint32_t lo = i - 3;
+    const bool disjoint = J[0] < lo && J[1] < lo && J[2] < lo && J[3] < lo && J[0] != J[1] &&
+                          J[0] != J[2] && J[0] != J[3] && J[1] != J[2] && J[1] != J[3] && J[2] != J[3];
+    if (disjoint) {
+        const L v0 = a[i], v1 = a[i - 1], v2 = a[i - 2], v3 = a[i - 3];
+        const L u0 = a[J[0]], u1 = a[J[1]], u2 = a[J[2]], u3 = a[J[3]];
+        a[i] = u0;
+        a[i - 1] = u1;
+        a[i - 2] = u2;
+        a[i - 3] = u3;
+        a[J[0]] = v0;
+        a[J[1]] = v1;
+        a[J[2]] = v2;
+        a[J[3]] = v3;
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t ii = i - t;
+            const L ai = a[ii];
+            a[ii] = a[J[t]];
+            a[J[t]] = ai;
+        }
+    }
+}
+
 // The row's shuffle.  Draw w of the stream is word w % 4 of block w / 4, and
 // step j's range is i + 1.  Steps go in groups of four while the stream is at
 // a block boundary: one block gives the group's four draws, and when none of
@@ -294,13 +329,7 @@ __device__ __forceinline__ void shuffle_row(L* a, uint32_t n, uint64_t seed, uin
                 uint32_t y[4];
                 const bool next = i >= 8;
                 if (next) philox_block(k0, k1, (w >> 2) + 1, p, y);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t ii = i - q;
-                    const L ai = a[ii];
-                    a[ii] = a[J[q]];
-                    a[J[q]] = ai;
-                }
+                swap4(a, i, J);
                 i -= 4;
                 w += 4;
                 if (next) {
@@ -367,6 +396,203 @@ k_shuffle_staged(uint32_t n, uint64_t total, uint32_t rows, const int32_t* __res
             out[s_dst[r] + c] = buf[(uint64_t)r * n + c];
 }
 
+// Warp path (long rows, fewer than FY_LANE_ROWS_MIN to a block): one warp per
+// row, the row in shared memory.  With a thread per row, the few rows a block
+// holds would sit on the lanes of one warp, every step a chain of dependent
+// instructions (Philox rounds, multiplies, checks, swaps) with no other warp
+// to hide it.  Here lane 0 walks the steps and the 32 lanes prepare them
+// together: at each refill lane l computes Philox block blk0 + l of the row's
+// stream (draws 4 blk0 + 4l .. +3) and, assuming no rejection between the
+// refill and its draws, the four steps those draws serve: their swap targets,
+// whether any draw needs Lemire's rejection check, and whether the four swaps
+// touch disjoint positions.  Without a rejection, i + w (step index plus draws
+// consumed) stays constant, so lane 0 uses a prepared group exactly when
+// i + w still equals its value at the refill; otherwise (after a rejection)
+// it computes the group from the buffered draws, and any step whose draw
+// needs the check runs alone with the same checks as the plain loop (a
+// rejection run past the buffer computes its blocks directly).  The rows are
+// bit-identical to the other paths.
+constexpr uint32_t FY_WORDS = 128;             // draws buffered per refill (32 lanes x 4)
+constexpr uint32_t FY_WARP_BYTES = FY_WORDS * 4 + FY_WORDS * 4 + 32 * 4;   // draws, targets, flags
+constexpr uint32_t FY_LANE_ROWS_MIN = 24;      // fewer rows to a block: the warp path
+constexpr uint32_t FY_OK = 1u, FY_DISJOINT = 2u;
+constexpr uint64_t FY_GLOBAL_RATIO = 8;       // rows / warp-path residency from which HBM wins
+constexpr uint64_t FY_GLOBAL_MAX_FIT = 3;     // ... for rows that fit at most this many to a block
+
+// Lane 0's steps on buffered draws [wbase, wbase + FY_WORDS) of the stream,
+// from step i (range i + 1) and draw w, until the row is done or the next
+// step's first draw lies beyond the buffer.  wj / wf: the lanes' prepared
+// targets and flags, valid while i + w == inv.
+template <typename L>
+__device__ __forceinline__ void fy_steps(L* a, const uint32_t* wb, const uint32_t* wj,
+                                         const uint32_t* wf, uint32_t wbase, uint32_t inv,
+                                         uint32_t& i_, uint32_t& w_, uint32_t k0, uint32_t k1,
+                                         uint32_t p) {
+    uint32_t i = i_, w = w_;
+    const uint32_t wend = wbase + FY_WORDS;
+    while (i >= 1 && w < wend) {
+        if ((w & 3u) == 0 && i >= 4 && w + 4 <= wend) {
+            if (i + w == inv) {
+                // prepared groups; the next group's targets are read before
+                // this group's swaps
+                uint32_t gq = (w - wbase) >> 2;
+                uint4 jq = *reinterpret_cast<const uint4*>(wj + 4 * gq);
+                uint32_t fl = wf[gq];
+                while ((fl & FY_OK) && i >= 4) {
+                    const uint32_t J[4] = {jq.x, jq.y, jq.z, jq.w};
+                    const uint32_t fcur = fl;
+                    const bool more = gq + 1 < FY_WORDS / 4;
+                    if (more) {
+                        jq = *reinterpret_cast<const uint4*>(wj + 4 * (gq + 1));
+                        fl = wf[gq + 1];
+                    }
+                    if (fcur & FY_DISJOINT) {
+                        const L v0 = a[i], v1 = a[i - 1], v2 = a[i - 2], v3 = a[i - 3];
+                        const L u0 = a[J[0]], u1 = a[J[1]], u2 = a[J[2]], u3 = a[J[3]];
+                        a[i] = u0;
+                        a[i - 1] = u1;
+                        a[i - 2] = u2;
+                        a[i - 3] = u3;
+                        a[J[0]] = v0;
+                        a[J[1]] = v1;
+                        a[J[2]] = v2;
+                        a[J[3]] = v3;
+                    } else {
+                        swap4(a, i, J);
+                    }
+                    i -= 4;
+                    w += 4;
+                    ++gq;
+                    if (!more) break;
+                }
+                if (w >= wend || i < 1) break;
+                if ((w & 3u) == 0 && i >= 4 && i + w == inv && !(wf[(w - wbase) >> 2] & FY_OK)) {
+                    // the prepared group needs the rejection check: one plain step below
+                } else {
+                    continue;
+                }
+            } else {
+                // after a rejection: the group from the buffered draws
+                const uint4 q = *reinterpret_cast<const uint4*>(wb + (w - wbase));
+                const uint32_t xs[4] = {q.x, q.y, q.z, q.w};
+                uint32_t J[4];
+                bool ok = true;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint64_t m = (uint64_t)xs[t] * (uint64_t)(i + 1 - t);
+                    J[t] = (uint32_t)(m >> 32);
+                    ok = ok && (uint32_t)m >= i + 1 - t;
+                }
+                if (ok) {
+                    swap4(a, i, J);
+                    i -= 4;
+                    w += 4;
+                    continue;
+                }
+            }
+        }
+        const uint32_t range = i + 1;
+        uint64_t m = (uint64_t)wb[w - wbase] * range;
+        ++w;
+        if ((uint32_t)m < range) {
+            const uint32_t thresh = (0u - range) % range;
+            while ((uint32_t)m < thresh) {
+                uint32_t x;
+                if (w < wend) {
+                    x = wb[w - wbase];
+                } else {
+                    uint32_t z[4];
+                    philox_block(k0, k1, w >> 2, p, z);
+                    x = z[w & 3u];
+                }
+                m = (uint64_t)x * range;
+                ++w;
+            }
+        }
+        const uint32_t j = (uint32_t)(m >> 32);
+        const L ai = a[i];
+        a[i] = a[j];
+        a[j] = ai;
+        --i;
+    }
+    i_ = i;
+    w_ = w;
+}
+
+// Block b shuffles permutation indices [b rows, (b+1) rows), rows <= 32, one
+// warp each; dynamic shared memory: each warp's draws, targets and flags,
+// then the rows.
+template <typename L, typename Rows>
+__global__ void __launch_bounds__(1024)
+k_shuffle_warp(uint32_t n, uint64_t total, uint32_t rows, const int32_t* __restrict__ g,
+               L* __restrict__ out, Rows map) {
+    extern __shared__ __align__(16) uint8_t fy_smem[];
+    L* buf = reinterpret_cast<L*>(fy_smem + (size_t)rows * FY_WARP_BYTES);   // [rows][n]
+    __shared__ uint64_t s_src[32], s_dst[32], s_seed[32];
+    __shared__ uint32_t s_p[32];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t idx0 = (uint64_t)blockIdx.x * rows;
+    const uint32_t nr = (uint32_t)min((uint64_t)rows, total - idx0);
+    if (threadIdx.x < nr) {
+        uint32_t p;
+        uint64_t seed, src, dst;
+        map.get(idx0 + threadIdx.x, p, seed, src, dst);
+        s_src[threadIdx.x] = src * n;
+        s_dst[threadIdx.x] = dst * n;
+        s_seed[threadIdx.x] = seed;
+        s_p[threadIdx.x] = p;
+    }
+    __syncthreads();
+    for (uint32_t r = 0; r < nr; ++r)
+        for (uint32_t c = threadIdx.x; c < n; c += blockDim.x)
+            buf[(uint64_t)r * n + c] = (L)g[s_src[r] + c];
+    __syncthreads();
+    if (warp < nr) {
+        L* a = buf + (uint64_t)warp * n;
+        uint32_t* wb = reinterpret_cast<uint32_t*>(fy_smem + (size_t)warp * FY_WARP_BYTES);
+        uint32_t* wj = wb + FY_WORDS;
+        uint32_t* wf = wj + FY_WORDS;
+        const uint64_t seed = s_seed[warp];
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), p = s_p[warp];
+        uint32_t i = n - 1, w = 0;
+        while (i >= 1) {                     // i and w are warp-uniform (lane 0's)
+            const uint32_t blk0 = w >> 2;
+            const uint32_t inv = i + w;
+            uint32_t x[4];
+            philox_block(k0, k1, blk0 + lane, p, x);
+            *reinterpret_cast<uint4*>(wb + 4 * lane) = make_uint4(x[0], x[1], x[2], x[3]);
+            // this lane's group: steps il .. il - 3 on draws 4 (blk0 + lane) .. +3
+            const uint32_t w4 = 4 * (blk0 + lane);
+            uint32_t flags = 0, J[4] = {0u, 0u, 0u, 0u};
+            if (w4 >= w && w4 + 4 <= inv) {
+                const uint32_t il = inv - w4;
+                bool ok = true;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint64_t m = (uint64_t)x[t] * (uint64_t)(il + 1 - t);
+                    J[t] = (uint32_t)(m >> 32);
+                    ok = ok && (uint32_t)m >= il + 1 - t;
+                }
+                const uint32_t lo = il - 3;
+                const bool dis = J[0] < lo && J[1] < lo && J[2] < lo && J[3] < lo && J[0] != J[1] &&
+                                 J[0] != J[2] && J[0] != J[3] && J[1] != J[2] && J[1] != J[3] && J[2] != J[3];
+                flags = (ok ? FY_OK : 0u) | (dis ? FY_DISJOINT : 0u);
+            }
+            *reinterpret_cast<uint4*>(wj + 4 * lane) = make_uint4(J[0], J[1], J[2], J[3]);
+            wf[lane] = flags;
+            __syncwarp();
+            if (lane == 0) fy_steps(a, wb, wj, wf, 4 * blk0, inv, i, w, k0, k1, p);
+            __syncwarp();
+            i = __shfl_sync(0xffffffffu, i, 0);
+            w = __shfl_sync(0xffffffffu, w, 0);
+        }
+    }
+    __syncthreads();
+    for (uint32_t r = 0; r < nr; ++r)
+        for (uint32_t c = threadIdx.x; c < n; c += blockDim.x)
+            out[s_dst[r] + c] = buf[(uint64_t)r * n + c];
+}
+
 // Global path: one thread per permutation index, its row already holding the
 // observed labels.
 template <typename L, typename Rows>
@@ -410,25 +636,53 @@ static int device_sms() {
         sms = 152;
     return sms;
 }
-// Rows per staged block: as many as fit (at most 128) and no more than an even
-// spread over the SMs needs; 0 selects the global path (fewer than 4 fit).
-static uint32_t staged_rows(uint32_t n, size_t elem, uint64_t total) {
-    const uint64_t fit = FY_SMEM_MAX / ((uint64_t)n * elem);
-    if (fit < 4) return 0;
+// Where the rows are shuffled.  A block takes as many rows as fit its shared
+// memory and no more than an even spread over the SMs needs: with at least
+// FY_LANE_ROWS_MIN of them, a thread per row (staged path); with fewer, a warp
+// per row (warp path, at most 32).  When not one row fits, and for very long
+// rows (at most FY_GLOBAL_MAX_FIT to a block) when the rows to shuffle number
+// FY_GLOBAL_RATIO times what the warp path holds on the GPU at once, they are
+// shuffled in place in HBM (global path, rows == 0): every row runs at once,
+// a step's latency an HBM round trip per four steps.  Measured alone (uint8
+// rows, ms): n = 15,000 / 9,999 rows: warp 3.9, global 4.7; 30,000 / 9,999:
+// 9.8, 10.5; 60,000 / 9,999: 41.6, 23.2; 100,000 / 8,191: 84.9, 35.4;
+// 100,000 / 999: 12.4, 16.7.  Beside other kernels (a server's fused
+// batches) the global path fares worse: taken for every row count above 10x
+// the warp path's residency, it cut a served mix's capacity by 14 %.
+struct FyPlan {
+    uint32_t rows;
+    bool warp;
+};
+static FyPlan fy_plan(uint32_t n, size_t elem, uint64_t total) {
     const int sms = device_sms();
-    const uint64_t spread = (total + (uint64_t)sms - 1) / (uint64_t)sms;
-    uint64_t r = fit < FY_THREADS ? fit : FY_THREADS;
-    if (spread < r) r = spread ? spread : 1;
-    return (uint32_t)r;
+    uint64_t spread = (total + (uint64_t)sms - 1) / (uint64_t)sms;
+    if (spread < 1) spread = 1;
+    const uint64_t fit = FY_SMEM_MAX / ((uint64_t)n * elem);
+    const uint64_t r_lane = std::min<uint64_t>(std::min<uint64_t>(fit, FY_THREADS), spread);
+    if (r_lane >= FY_LANE_ROWS_MIN) return FyPlan{(uint32_t)r_lane, false};
+    const uint64_t fit_w = FY_SMEM_MAX / ((uint64_t)n * elem + FY_WARP_BYTES);
+    if (fit_w == 0) return FyPlan{0u, false};
+    if (fit_w <= FY_GLOBAL_MAX_FIT && total >= FY_GLOBAL_RATIO * fit_w * (uint64_t)sms)
+        return FyPlan{0u, false};
+    return FyPlan{(uint32_t)std::min<uint64_t>(std::min<uint64_t>(fit_w, 32), spread), true};
 }
 
-// The shuffles of `total` permutation rows; `rows` from staged_rows (the global
+// The shuffles of `total` permutation rows by the plan from fy_plan (the global
 // path's rows must already hold the observed labels).
 template <typename L, typename Rows>
 static cudaError_t launch_shuffles(uint32_t n, uint64_t total, const int32_t* g, L* out, Rows map,
-                                   uint32_t rows, cudaStream_t s) {
+                                   FyPlan pl, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
-    if (rows) {
+    const uint32_t rows = pl.rows;
+    if (rows && pl.warp) {
+        const size_t smem = (size_t)rows * (FY_WARP_BYTES + (size_t)n * sizeof(L));
+        cudaError_t e = cudaFuncSetAttribute(k_shuffle_warp<L, Rows>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const uint64_t blocks = (total + rows - 1) / rows;
+        if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+        k_shuffle_warp<L, Rows><<<(unsigned)blocks, 32 * rows, smem, s>>>(n, total, rows, g, out, map);
+    } else if (rows) {
         const size_t smem = (size_t)rows * n * sizeof(L);
         cudaError_t e = cudaFuncSetAttribute(k_shuffle_staged<L, Rows>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -453,10 +707,11 @@ static cudaError_t launch_shuffles(uint32_t n, uint64_t total, const int32_t* g,
 template <typename L>
 static cudaError_t permutations_t(const int32_t* grouping, uint32_t n, uint64_t n_perms, uint64_t seed,
                                   L* out, cudaStream_t s) {
-    const uint32_t rows = staged_rows(n, sizeof(L), n_perms);
-    // staged: only the observed row is copied; global: every row, then shuffled in place
-    k_copy_grouping<L><<<152 * 8, 256, 0, s>>>(grouping, n, rows ? 1 : n_perms + 1, out);
-    return launch_shuffles<L>(n, n_perms, grouping, out, SingleRows{seed}, rows, s);
+    const FyPlan pl = fy_plan(n, sizeof(L), n_perms);
+    // staged and warp paths: only the observed row is copied; global: every
+    // row, then shuffled in place
+    k_copy_grouping<L><<<152 * 8, 256, 0, s>>>(grouping, n, pl.rows ? 1 : n_perms + 1, out);
+    return launch_shuffles<L>(n, n_perms, grouping, out, SingleRows{seed}, pl, s);
 }
 
 cudaError_t launch_permutations(const int32_t* grouping, uint32_t n, uint64_t n_perms,
@@ -475,10 +730,10 @@ template <typename L>
 static cudaError_t perms_batch_t(const int32_t* g, const uint32_t* src, uint32_t n, uint32_t n_tests,
                                  const uint64_t* rs, uint64_t total_perms, const uint64_t* seeds, L* out,
                                  cudaStream_t s) {
-    const uint32_t rows = staged_rows(n, sizeof(L), total_perms);
+    const FyPlan pl = fy_plan(n, sizeof(L), total_perms);
     const dim3 cgrid(152 * 2, n_tests < 65535u ? n_tests : 65535u);
-    k_copy_groupings<L><<<cgrid, 256, 0, s>>>(g, src, n, n_tests, rs, rows == 0, out);
-    return launch_shuffles<L>(n, total_perms, g, out, BatchRows{rs, seeds, src, n_tests}, rows, s);
+    k_copy_groupings<L><<<cgrid, 256, 0, s>>>(g, src, n, n_tests, rs, pl.rows == 0, out);
+    return launch_shuffles<L>(n, total_perms, g, out, BatchRows{rs, seeds, src, n_tests}, pl, s);
 }
 
 cudaError_t launch_permutations_batch(const int32_t* groupings, const uint32_t* src, uint32_t n,

@@ -276,9 +276,9 @@ def test_permutations_bit_exact_with_oracle(ctx):
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 9, 16, 17, 1000, 5003, 50000, 60000])
 def test_permutations_bit_exact_across_row_lengths(ctx, n):
-    """Short and long rows, shuffled in shared memory (rows that fit four or
-    more to a block) or in place in HBM (n = 60,000: three uint8 rows or no
-    int32 row fit): every row equals the oracle's Fisher-Yates shuffle.  At
+    """Short and long rows (40 of them: a warp per row in shared memory, or
+    in place in HBM when not one int32 row fits, n = 60,000): every row
+    equals the oracle's Fisher-Yates shuffle.  At
     n >= 50,000 some draws need Lemire's rejection check (about 0.3 draws per
     row at 50,000, 0.4 at 60,000), which the shuffle takes one at a time."""
     K = 2 if n < 8 else 5
@@ -288,6 +288,32 @@ def test_permutations_bit_exact_across_row_lengths(ctx, n):
         pm.permanova_permutations(ctx.handle, _dev(obs), n, K, 40, 77 + n, out, ltype)
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.permutations(obs, 40, 77 + n))
+
+
+@pytest.mark.parametrize("n,P,seed", [(1000, 4000, 5), (30000, 999, 6), (60000, 4000, 8),
+                                       (100000, 80, 424242)])
+def test_permutations_every_shuffle_path(ctx, n, P, seed):
+    """Each way the shuffles run gives the oracle's rows bit for bit: a thread
+    per row in shared memory (n = 1,000, 4,000 rows: 27 rows to a block), a
+    warp per row in shared memory (n = 30,000: 7 uint8 rows or 1 int32 row to
+    a block; n = 100,000 uint8: 1 row), in place in HBM (n = 60,000 with 4,000
+    rows, more than eight times what the warp path holds at once; n = 100,000
+    int32, where not one row fits).  In the last case row 80's stream has a
+    rejection at draw 5,503, the last of a 128-draw buffer of the warp path,
+    whose second draw lies past the buffer (found by a search over rows; the
+    first draw is checked here)."""
+    obs = synth.observed_labels([n // 3, n // 3, n - 2 * (n // 3)], seed)
+    if seed == 424242:
+        x = oracle.philox4x32_10([5503 // 4, 0, 80, 0], [seed & 0xFFFFFFFF, seed >> 32])[5503 % 4]
+        rng = 94497                          # step i = 94,496 draws from [0, i]
+        low = (int(x) * rng) & 0xFFFFFFFF
+        assert low < (2**32 - rng) % rng     # Lemire rejects this draw
+    ref = oracle.permutations(obs, P, seed)
+    for ltype, tdt in ((pm.LABEL_U8, torch.uint8), (pm.LABEL_I32, torch.int32)):
+        out = torch.empty((P + 1, n), dtype=tdt, device="cuda")
+        pm.permanova_permutations(ctx.handle, _dev(obs), n, 3, P, seed, out, ltype)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), ref)
 
 
 @pytest.mark.parametrize("n,K,P,seed", [(60, 2, 99, 1), (257, 3, 999, 2), (1000, 3, 999, 3)])

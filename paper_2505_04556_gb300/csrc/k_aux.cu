@@ -211,14 +211,13 @@ struct Philox4x32 {
 // takes n dependent steps; where the row lives and what sits on a step's
 // chain decide their latency (fy_plan picks the path).
 //
-// Staged path (short rows, many to a block): a block copies the observed
-// labels of up to 128 rows into shared memory, each thread shuffles its row
-// there (a step is a few shared-memory accesses), and the block writes the
-// rows back coalesced.  Warp path (long rows, or few): the same with a warp
-// per row, its lanes preparing the draws and swap targets (k_shuffle_warp).
-// Global path (rows too long for shared memory): each thread shuffles its row
-// in place in HBM (the rows copied there first); every step then waits on an
-// L2 or DRAM round trip.
+// Shared-memory path (k_shuffle_warp): a block copies the observed labels of
+// up to 128 rows into shared memory, one to four rows to a warp; one lane per
+// row walks its steps there (a step is a few shared-memory accesses) while
+// the row's other lanes prepare the draws and swap targets, and the block
+// writes the rows back coalesced.  Global path (rows too long for shared
+// memory): each thread shuffles its row in place in HBM (the rows copied
+// there first); every step then waits on an L2 or DRAM round trip.
 //
 // Rows of a batch map to (test, p) by the tests' row starts: test t owns rows
 // [rs[t], rs[t+1]) of the output, the first its observed grouping (row src[t]
@@ -363,90 +362,56 @@ __device__ __forceinline__ void shuffle_row(L* a, uint32_t n, uint64_t seed, uin
     }
 }
 
-constexpr uint32_t FY_THREADS = 128;                 // threads of a staged block (rows <= this)
-constexpr uint32_t FY_SMEM_MAX = 220u * 1024u;       // shared memory for a staged block's rows
+constexpr uint32_t FY_SMEM_MAX = 220u * 1024u;       // shared memory for a block's rows
 
-// Staged path: block b shuffles permutation indices [b rows, (b+1) rows).
-template <typename L, typename Rows>
-__global__ void __launch_bounds__(FY_THREADS)
-k_shuffle_staged(uint32_t n, uint64_t total, uint32_t rows, const int32_t* __restrict__ g,
-                 L* __restrict__ out, Rows map) {
-    extern __shared__ __align__(16) uint8_t fy_smem[];
-    L* buf = reinterpret_cast<L*>(fy_smem);          // [rows][n]
-    __shared__ uint64_t s_src[FY_THREADS], s_dst[FY_THREADS];
-    const uint64_t idx0 = (uint64_t)blockIdx.x * rows;
-    const uint32_t nr = (uint32_t)min((uint64_t)rows, total - idx0);
-    uint32_t p = 0;
-    uint64_t seed = 0;
-    if (threadIdx.x < nr) {
-        uint64_t src, dst;
-        map.get(idx0 + threadIdx.x, p, seed, src, dst);
-        s_src[threadIdx.x] = src * n;
-        s_dst[threadIdx.x] = dst * n;
-    }
-    __syncthreads();
-    for (uint32_t r = 0; r < nr; ++r)
-        for (uint32_t c = threadIdx.x; c < n; c += FY_THREADS)
-            buf[(uint64_t)r * n + c] = (L)g[s_src[r] + c];
-    __syncthreads();
-    if (threadIdx.x < nr) shuffle_row(buf + (uint64_t)threadIdx.x * n, n, seed, p);
-    __syncthreads();
-    for (uint32_t r = 0; r < nr; ++r)
-        for (uint32_t c = threadIdx.x; c < n; c += FY_THREADS)
-            out[s_dst[r] + c] = buf[(uint64_t)r * n + c];
-}
-
-// Warp path (long rows, fewer than FY_LANE_ROWS_MIN to a block): one warp per
-// row, the row in shared memory.  With a thread per row, the few rows a block
-// holds would sit on the lanes of one warp, every step a chain of dependent
-// instructions (Philox rounds, multiplies, checks, swaps) with no other warp
-// to hide it.  Here lane 0 walks the steps and the 32 lanes prepare them
-// together: at each refill lane l computes Philox block blk0 + l of the row's
-// stream (draws 4 blk0 + 4l .. +3) and, assuming no rejection between the
-// refill and its draws, the four steps those draws serve: their swap targets,
-// whether any draw needs Lemire's rejection check, and whether the four swaps
-// touch disjoint positions.  Without a rejection, i + w (step index plus draws
-// consumed) stays constant, so lane 0 uses a prepared group exactly when
-// i + w still equals its value at the refill; otherwise (after a rejection)
-// it computes the group from the buffered draws, and any step whose draw
-// needs the check runs alone with the same checks as the plain loop (a
-// rejection run past the buffer computes its blocks directly).  The rows are
-// bit-identical to the other paths.
-constexpr uint32_t FY_WORDS = 128;             // draws buffered per refill (32 lanes x 4)
-constexpr uint32_t FY_WARP_BYTES = FY_WORDS * 4 + FY_WORDS * 4 + 32 * 4;   // draws, targets, flags
-constexpr uint32_t FY_LANE_ROWS_MIN = 24;      // fewer rows to a block: the warp path
-constexpr uint32_t FY_OK = 1u, FY_DISJOINT = 2u;
+// Shared-memory path: one to four rows per warp, each with 32 / RPW lanes,
+// the rows in shared memory.  With a thread per row, a block's rows would sit
+// on the lanes of a few warps, every step a chain of dependent instructions
+// (Philox rounds, multiplies, checks, swaps) with few other warps to hide it,
+// and the lanes' rows would share banks.  Here the first lane of each
+// row's group walks the row's steps and the group prepares them: at each
+// refill the row's next Philox blocks (32 blocks, 128 draws, for a row alone in
+// its warp, else 16 blocks, 64 draws) are computed and, assuming
+// no rejection since the refill, for each block the swap targets of the four
+// steps its draws serve, whether any of the draws needs Lemire's rejection
+// check (FY_OK clear) and whether the four swaps touch disjoint positions
+// (FY_DISJOINT); both flags ride in the top bits of the first target (n <
+// 2^30 here).  Without a rejection, i + w (step index plus draws consumed)
+// stays constant, so the walker uses a prepared group exactly while i + w
+// equals its value at the refill.  Off that path (a step whose draw needs the
+// check, the steps after a rejection up to the next refill, the last three
+// steps) the walker computes its draws from the Philox blocks itself, one at
+// a time exactly as the plain loop.  The rows are bit-identical to the other
+// paths.
+// draws prepared per refill (a row's targets and flags take 4 bytes a draw)
+__host__ __device__ constexpr uint32_t fy_words(int rpw) { return rpw == 1 ? 128u : 64u; }
+constexpr uint32_t FY_ROWS_MAX = 128;          // rows of a warp-path block (4 to a warp)
+constexpr uint32_t FY_OK = 1u << 31, FY_DISJOINT = 1u << 30, FY_J = FY_DISJOINT - 1u;
 constexpr uint64_t FY_GLOBAL_RATIO = 8;       // rows / warp-path residency from which HBM wins
 constexpr uint64_t FY_GLOBAL_MAX_FIT = 3;     // ... for rows that fit at most this many to a block
 
-// Lane 0's steps on buffered draws [wbase, wbase + FY_WORDS) of the stream,
-// from step i (range i + 1) and draw w, until the row is done or the next
-// step's first draw lies beyond the buffer.  wj / wf: the lanes' prepared
-// targets and flags, valid while i + w == inv.
-template <typename L>
-__device__ __forceinline__ void fy_steps(L* a, const uint32_t* wb, const uint32_t* wj,
-                                         const uint32_t* wf, uint32_t wbase, uint32_t inv,
+// The walker's steps while its draws lie in [wbase, wbase + WORDS): from
+// step i (range i + 1) and draw w until the row is done or the next step's
+// first draw lies beyond.  wj: the prepared groups, valid while i + w == inv.
+template <typename L, uint32_t WORDS>
+__device__ __forceinline__ void fy_steps(L* a, const uint32_t* wj, uint32_t wbase, uint32_t inv,
                                          uint32_t& i_, uint32_t& w_, uint32_t k0, uint32_t k1,
                                          uint32_t p) {
     uint32_t i = i_, w = w_;
-    const uint32_t wend = wbase + FY_WORDS;
+    const uint32_t wend = wbase + WORDS;
+    uint32_t zb = 0xFFFFFFFFu, z[4];             // Philox block zb, computed on demand
     while (i >= 1 && w < wend) {
         if ((w & 3u) == 0 && i >= 4 && w + 4 <= wend) {
             if (i + w == inv) {
-                // prepared groups; the next group's targets are read before
-                // this group's swaps
+                // prepared groups; the next group is read before this group's swaps
                 uint32_t gq = (w - wbase) >> 2;
                 uint4 jq = *reinterpret_cast<const uint4*>(wj + 4 * gq);
-                uint32_t fl = wf[gq];
-                while ((fl & FY_OK) && i >= 4) {
-                    const uint32_t J[4] = {jq.x, jq.y, jq.z, jq.w};
-                    const uint32_t fcur = fl;
-                    const bool more = gq + 1 < FY_WORDS / 4;
-                    if (more) {
-                        jq = *reinterpret_cast<const uint4*>(wj + 4 * (gq + 1));
-                        fl = wf[gq + 1];
-                    }
-                    if (fcur & FY_DISJOINT) {
+                while ((jq.x & FY_OK) && i >= 4) {
+                    const uint32_t J[4] = {jq.x & FY_J, jq.y, jq.z, jq.w};
+                    const bool dis = (jq.x & FY_DISJOINT) != 0;
+                    const bool more = gq + 1 < WORDS / 4;
+                    if (more) jq = *reinterpret_cast<const uint4*>(wj + 4 * (gq + 1));
+                    if (dis) {
                         const L v0 = a[i], v1 = a[i - 1], v2 = a[i - 2], v3 = a[i - 3];
                         const L u0 = a[J[0]], u1 = a[J[1]], u2 = a[J[2]], u3 = a[J[3]];
                         a[i] = u0;
@@ -466,20 +431,17 @@ __device__ __forceinline__ void fy_steps(L* a, const uint32_t* wb, const uint32_
                     if (!more) break;
                 }
                 if (w >= wend || i < 1) break;
-                if ((w & 3u) == 0 && i >= 4 && i + w == inv && !(wf[(w - wbase) >> 2] & FY_OK)) {
-                    // the prepared group needs the rejection check: one plain step below
-                } else {
-                    continue;
-                }
+                if (!((w & 3u) == 0 && i >= 4 && i + w == inv && !(wj[w - wbase] & FY_OK))) continue;
+                // else: this group's draws need the check; one plain step below
             } else {
-                // after a rejection: the group from the buffered draws
-                const uint4 q = *reinterpret_cast<const uint4*>(wb + (w - wbase));
-                const uint32_t xs[4] = {q.x, q.y, q.z, q.w};
+                // after a rejection: the group from its Philox block
+                uint32_t x[4];
+                philox_block(k0, k1, w >> 2, p, x);
                 uint32_t J[4];
                 bool ok = true;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const uint64_t m = (uint64_t)xs[t] * (uint64_t)(i + 1 - t);
+                    const uint64_t m = (uint64_t)x[t] * (uint64_t)(i + 1 - t);
                     J[t] = (uint32_t)(m >> 32);
                     ok = ok && (uint32_t)m >= i + 1 - t;
                 }
@@ -492,20 +454,20 @@ __device__ __forceinline__ void fy_steps(L* a, const uint32_t* wb, const uint32_
             }
         }
         const uint32_t range = i + 1;
-        uint64_t m = (uint64_t)wb[w - wbase] * range;
+        if (zb != (w >> 2)) {
+            zb = w >> 2;
+            philox_block(k0, k1, zb, p, z);
+        }
+        uint64_t m = (uint64_t)z[w & 3u] * range;
         ++w;
         if ((uint32_t)m < range) {
             const uint32_t thresh = (0u - range) % range;
             while ((uint32_t)m < thresh) {
-                uint32_t x;
-                if (w < wend) {
-                    x = wb[w - wbase];
-                } else {
-                    uint32_t z[4];
-                    philox_block(k0, k1, w >> 2, p, z);
-                    x = z[w & 3u];
+                if (zb != (w >> 2)) {
+                    zb = w >> 2;
+                    philox_block(k0, k1, zb, p, z);
                 }
-                m = (uint64_t)x * range;
+                m = (uint64_t)z[w & 3u] * range;
                 ++w;
             }
         }
@@ -519,18 +481,23 @@ __device__ __forceinline__ void fy_steps(L* a, const uint32_t* wb, const uint32_
     w_ = w;
 }
 
-// Block b shuffles permutation indices [b rows, (b+1) rows), rows <= 32, one
-// warp each; dynamic shared memory: each warp's draws, targets and flags,
-// then the rows.
-template <typename L, typename Rows>
+// Block b shuffles permutation indices [b rows, (b+1) rows), RPW rows to a
+// warp (rows <= 32 RPW), row r of the block at r * ns in shared memory after
+// the rows' prepared groups.  The walkers of one warp advance together (their
+// rows have the same length).
+template <typename L, typename Rows, int RPW>
 __global__ void __launch_bounds__(1024)
-k_shuffle_warp(uint32_t n, uint64_t total, uint32_t rows, const int32_t* __restrict__ g,
+k_shuffle_warp(uint32_t n, uint32_t ns, uint64_t total, uint32_t rows, const int32_t* __restrict__ g,
                L* __restrict__ out, Rows map) {
+    constexpr uint32_t HL = 32 / RPW;            // lanes per row
+    constexpr uint32_t WORDS = fy_words(RPW);
     extern __shared__ __align__(16) uint8_t fy_smem[];
-    L* buf = reinterpret_cast<L*>(fy_smem + (size_t)rows * FY_WARP_BYTES);   // [rows][n]
-    __shared__ uint64_t s_src[32], s_dst[32], s_seed[32];
-    __shared__ uint32_t s_p[32];
+    L* buf = reinterpret_cast<L*>(fy_smem + (size_t)rows * WORDS * 4);   // [rows][ns]
+    __shared__ uint64_t s_src[FY_ROWS_MAX], s_dst[FY_ROWS_MAX], s_seed[FY_ROWS_MAX];
+    __shared__ uint32_t s_p[FY_ROWS_MAX];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t h = lane % HL, walker = lane - h;   // helper index, the group's first lane
+    const uint32_t row = warp * RPW + lane / HL;
     const uint64_t idx0 = (uint64_t)blockIdx.x * rows;
     const uint32_t nr = (uint32_t)min((uint64_t)rows, total - idx0);
     if (threadIdx.x < nr) {
@@ -545,52 +512,55 @@ k_shuffle_warp(uint32_t n, uint64_t total, uint32_t rows, const int32_t* __restr
     __syncthreads();
     for (uint32_t r = 0; r < nr; ++r)
         for (uint32_t c = threadIdx.x; c < n; c += blockDim.x)
-            buf[(uint64_t)r * n + c] = (L)g[s_src[r] + c];
+            buf[(uint64_t)r * ns + c] = (L)g[s_src[r] + c];
     __syncthreads();
-    if (warp < nr) {
-        L* a = buf + (uint64_t)warp * n;
-        uint32_t* wb = reinterpret_cast<uint32_t*>(fy_smem + (size_t)warp * FY_WARP_BYTES);
-        uint32_t* wj = wb + FY_WORDS;
-        uint32_t* wf = wj + FY_WORDS;
-        const uint64_t seed = s_seed[warp];
-        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), p = s_p[warp];
-        uint32_t i = n - 1, w = 0;
-        while (i >= 1) {                     // i and w are warp-uniform (lane 0's)
+    if (warp * RPW < nr) {
+        const bool active = row < nr;
+        const uint32_t rr = active ? row : 0;
+        L* a = buf + (uint64_t)rr * ns;
+        uint32_t* wj = reinterpret_cast<uint32_t*>(fy_smem + (size_t)rr * WORDS * 4);
+        const uint64_t seed = s_seed[rr];
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32), p = s_p[rr];
+        uint32_t i = active ? n - 1 : 0, w = 0;   // the row's step and draw (its walker's)
+        while (__any_sync(0xffffffffu, i >= 1)) {
             const uint32_t blk0 = w >> 2;
             const uint32_t inv = i + w;
-            uint32_t x[4];
-            philox_block(k0, k1, blk0 + lane, p, x);
-            *reinterpret_cast<uint4*>(wb + 4 * lane) = make_uint4(x[0], x[1], x[2], x[3]);
-            // this lane's group: steps il .. il - 3 on draws 4 (blk0 + lane) .. +3
-            const uint32_t w4 = 4 * (blk0 + lane);
-            uint32_t flags = 0, J[4] = {0u, 0u, 0u, 0u};
-            if (w4 >= w && w4 + 4 <= inv) {
-                const uint32_t il = inv - w4;
-                bool ok = true;
+            if (i >= 1) {
+                for (uint32_t b = h; b < WORDS / 4; b += HL) {   // this lane's blocks
+                    uint32_t x[4];
+                    philox_block(k0, k1, blk0 + b, p, x);
+                    // block b's group: steps il .. il - 3 on draws 4 (blk0 + b) .. +3
+                    const uint32_t w4 = 4 * (blk0 + b);
+                    uint32_t flags = 0, J[4] = {0u, 0u, 0u, 0u};
+                    if (w4 >= w && w4 + 4 <= inv) {
+                        const uint32_t il = inv - w4;
+                        bool ok = true;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const uint64_t m = (uint64_t)x[t] * (uint64_t)(il + 1 - t);
-                    J[t] = (uint32_t)(m >> 32);
-                    ok = ok && (uint32_t)m >= il + 1 - t;
+                        for (int t = 0; t < 4; ++t) {
+                            const uint64_t m = (uint64_t)x[t] * (uint64_t)(il + 1 - t);
+                            J[t] = (uint32_t)(m >> 32);
+                            ok = ok && (uint32_t)m >= il + 1 - t;
+                        }
+                        const uint32_t lo = il - 3;
+                        const bool dis = J[0] < lo && J[1] < lo && J[2] < lo && J[3] < lo && J[0] != J[1] &&
+                                         J[0] != J[2] && J[0] != J[3] && J[1] != J[2] && J[1] != J[3] &&
+                                         J[2] != J[3];
+                        flags = (ok ? FY_OK : 0u) | (dis ? FY_DISJOINT : 0u);
+                    }
+                    *reinterpret_cast<uint4*>(wj + 4 * b) = make_uint4(J[0] | flags, J[1], J[2], J[3]);
                 }
-                const uint32_t lo = il - 3;
-                const bool dis = J[0] < lo && J[1] < lo && J[2] < lo && J[3] < lo && J[0] != J[1] &&
-                                 J[0] != J[2] && J[0] != J[3] && J[1] != J[2] && J[1] != J[3] && J[2] != J[3];
-                flags = (ok ? FY_OK : 0u) | (dis ? FY_DISJOINT : 0u);
             }
-            *reinterpret_cast<uint4*>(wj + 4 * lane) = make_uint4(J[0], J[1], J[2], J[3]);
-            wf[lane] = flags;
             __syncwarp();
-            if (lane == 0) fy_steps(a, wb, wj, wf, 4 * blk0, inv, i, w, k0, k1, p);
+            if (h == 0 && i >= 1) fy_steps<L, WORDS>(a, wj, 4 * blk0, inv, i, w, k0, k1, p);
             __syncwarp();
-            i = __shfl_sync(0xffffffffu, i, 0);
-            w = __shfl_sync(0xffffffffu, w, 0);
+            i = __shfl_sync(0xffffffffu, i, walker);
+            w = __shfl_sync(0xffffffffu, w, walker);
         }
     }
     __syncthreads();
     for (uint32_t r = 0; r < nr; ++r)
         for (uint32_t c = threadIdx.x; c < n; c += blockDim.x)
-            out[s_dst[r] + c] = buf[(uint64_t)r * n + c];
+            out[s_dst[r] + c] = buf[(uint64_t)r * ns + c];
 }
 
 // Global path: one thread per permutation index, its row already holding the
@@ -636,35 +606,63 @@ static int device_sms() {
         sms = 152;
     return sms;
 }
-// Where the rows are shuffled.  A block takes as many rows as fit its shared
-// memory and no more than an even spread over the SMs needs: with at least
-// FY_LANE_ROWS_MIN of them, a thread per row (staged path); with fewer, a warp
-// per row (warp path, at most 32).  When not one row fits, and for very long
-// rows (at most FY_GLOBAL_MAX_FIT to a block) when the rows to shuffle number
-// FY_GLOBAL_RATIO times what the warp path holds on the GPU at once, they are
-// shuffled in place in HBM (global path, rows == 0): every row runs at once,
-// a step's latency an HBM round trip per four steps.  Measured alone (uint8
-// rows, ms): n = 15,000 / 9,999 rows: warp 3.9, global 4.7; 30,000 / 9,999:
-// 9.8, 10.5; 60,000 / 9,999: 41.6, 23.2; 100,000 / 8,191: 84.9, 35.4;
-// 100,000 / 999: 12.4, 16.7.  Beside other kernels (a server's fused
-// batches) the global path fares worse: taken for every row count above 10x
-// the warp path's residency, it cut a served mix's capacity by 14 %.
+// Where the rows are shuffled.  In shared memory (k_shuffle_warp), a block
+// taking as many rows as fit (at most FY_ROWS_MAX), then as few as keep the
+// same number of waves over the SMs.  When not one row fits, and for very
+// long rows (at most FY_GLOBAL_MAX_FIT to a block) when the rows to shuffle
+// number FY_GLOBAL_RATIO times what shared memory holds on the GPU at once,
+// in place in HBM (global path, rows == 0): every row runs at once, a step's
+// latency an HBM round trip per four steps.  Measured alone (uint8 rows,
+// ms): n = 15,000 / 9,999 rows: shared memory 3.1, global 4.7; 30,000 /
+// 9,999: 9.5, 10.5; 60,000 / 9,999: 41.6 (earlier shared-memory kernel),
+// 23.2; 100,000 / 8,191: 84.9 (earlier), 35.4; 100,000 / 999: 11.9, 16.7.
+// Beside other kernels (a server's fused batches) the global path fares
+// worse: taken for every row count above 10x the shared-memory residency, it
+// cut a served mix's capacity by 14 %.  A thread per row in shared memory
+// (the previous kernel) was slower at every size measured, up to 2.5x.
 struct FyPlan {
-    uint32_t rows;
-    bool warp;
+    uint32_t rows;  // rows to a block (0: the global path)
+    uint32_t rpw;   // rows to a warp (1, 2 or 4)
+    uint32_t ns;    // shared-memory row stride (elements)
 };
 static FyPlan fy_plan(uint32_t n, size_t elem, uint64_t total) {
     const int sms = device_sms();
     uint64_t spread = (total + (uint64_t)sms - 1) / (uint64_t)sms;
     if (spread < 1) spread = 1;
-    const uint64_t fit = FY_SMEM_MAX / ((uint64_t)n * elem);
-    const uint64_t r_lane = std::min<uint64_t>(std::min<uint64_t>(fit, FY_THREADS), spread);
-    if (r_lane >= FY_LANE_ROWS_MIN) return FyPlan{(uint32_t)r_lane, false};
-    const uint64_t fit_w = FY_SMEM_MAX / ((uint64_t)n * elem + FY_WARP_BYTES);
-    if (fit_w == 0) return FyPlan{0u, false};
+    // rows in shared memory start an odd number of 4-byte words apart, so the
+    // same position of up to 32 rows falls in 32 distinct banks
+    uint64_t words = ((uint64_t)n * elem + 3) / 4;
+    if ((words & 1u) == 0) ++words;
+    const uint64_t row_bytes = words * 4;
+    const uint32_t ns = (uint32_t)(row_bytes / elem);
+    // as many rows as fit (at most FY_ROWS_MAX), then as few as keep the same
+    // number of waves over the SMs, so the last wave is not a sliver
+    uint64_t fit_w = FY_SMEM_MAX / (row_bytes + 4 * fy_words(2));
+    if (fit_w <= 32) fit_w = FY_SMEM_MAX / (row_bytes + 4 * fy_words(1));   // a row alone in its warp
+    if (fit_w == 0) return FyPlan{0u, 0u, ns};
     if (fit_w <= FY_GLOBAL_MAX_FIT && total >= FY_GLOBAL_RATIO * fit_w * (uint64_t)sms)
-        return FyPlan{0u, false};
-    return FyPlan{(uint32_t)std::min<uint64_t>(std::min<uint64_t>(fit_w, 32), spread), true};
+        return FyPlan{0u, 0u, ns};
+    const uint64_t cap = std::min<uint64_t>(fit_w, FY_ROWS_MAX);
+    const uint64_t waves = (total + cap * sms - 1) / (cap * sms);
+    const uint64_t r64 = std::min<uint64_t>(cap, (total + waves * sms - 1) / (waves * sms));
+    uint32_t r = (uint32_t)std::max<uint64_t>(r64, 1);
+    auto rpw_of = [](uint32_t rows) { return rows <= 32 ? 1u : rows <= 64 ? 2u : 4u; };
+    while (r > 1 && (uint64_t)r * (row_bytes + 4 * fy_words((int)rpw_of(r))) > FY_SMEM_MAX) --r;
+    return FyPlan{r, rpw_of(r), ns};
+}
+
+template <typename L, typename Rows, int RPW>
+static cudaError_t launch_warp_path(uint32_t n, uint32_t ns, uint64_t total, const int32_t* g, L* out,
+                                    Rows map, uint32_t rows, cudaStream_t s) {
+    const size_t smem = (size_t)rows * (4 * fy_words(RPW) + (size_t)ns * sizeof(L));
+    cudaError_t e = cudaFuncSetAttribute(k_shuffle_warp<L, Rows, RPW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (total + rows - 1) / rows;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    const unsigned threads = 32u * ((rows + RPW - 1) / RPW);
+    k_shuffle_warp<L, Rows, RPW><<<(unsigned)blocks, threads, smem, s>>>(n, ns, total, rows, g, out, map);
+    return cudaSuccess;
 }
 
 // The shuffles of `total` permutation rows by the plan from fy_plan (the global
@@ -674,22 +672,11 @@ static cudaError_t launch_shuffles(uint32_t n, uint64_t total, const int32_t* g,
                                    FyPlan pl, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     const uint32_t rows = pl.rows;
-    if (rows && pl.warp) {
-        const size_t smem = (size_t)rows * (FY_WARP_BYTES + (size_t)n * sizeof(L));
-        cudaError_t e = cudaFuncSetAttribute(k_shuffle_warp<L, Rows>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (rows) {
+        cudaError_t e = pl.rpw == 4   ? launch_warp_path<L, Rows, 4>(n, pl.ns, total, g, out, map, rows, s)
+                        : pl.rpw == 2 ? launch_warp_path<L, Rows, 2>(n, pl.ns, total, g, out, map, rows, s)
+                                      : launch_warp_path<L, Rows, 1>(n, pl.ns, total, g, out, map, rows, s);
         if (e != cudaSuccess) return e;
-        const uint64_t blocks = (total + rows - 1) / rows;
-        if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-        k_shuffle_warp<L, Rows><<<(unsigned)blocks, 32 * rows, smem, s>>>(n, total, rows, g, out, map);
-    } else if (rows) {
-        const size_t smem = (size_t)rows * n * sizeof(L);
-        cudaError_t e = cudaFuncSetAttribute(k_shuffle_staged<L, Rows>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const uint64_t blocks = (total + rows - 1) / rows;
-        if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-        k_shuffle_staged<L, Rows><<<(unsigned)blocks, FY_THREADS, smem, s>>>(n, total, rows, g, out, map);
     } else {
         // one thread per row, the rows spread over every SM (a step's accesses
         // touch a different cache line in every lane): blocks of
@@ -708,7 +695,7 @@ template <typename L>
 static cudaError_t permutations_t(const int32_t* grouping, uint32_t n, uint64_t n_perms, uint64_t seed,
                                   L* out, cudaStream_t s) {
     const FyPlan pl = fy_plan(n, sizeof(L), n_perms);
-    // staged and warp paths: only the observed row is copied; global: every
+    // shared-memory path: only the observed row is copied; global: every
     // row, then shuffled in place
     k_copy_grouping<L><<<152 * 8, 256, 0, s>>>(grouping, n, pl.rows ? 1 : n_perms + 1, out);
     return launch_shuffles<L>(n, n_perms, grouping, out, SingleRows{seed}, pl, s);

@@ -290,18 +290,19 @@ def test_permutations_bit_exact_across_row_lengths(ctx, n):
         assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.permutations(obs, 40, 77 + n))
 
 
-@pytest.mark.parametrize("n,P,seed", [(1000, 4000, 5), (30000, 999, 6), (60000, 4000, 8),
-                                       (100000, 80, 424242)])
+@pytest.mark.parametrize("n,P,seed", [(1000, 4000, 5), (3000, 9999, 9), (4000, 9999, 10), (30000, 999, 6),
+                                       (60000, 4000, 8), (100000, 80, 424242)])
 def test_permutations_every_shuffle_path(ctx, n, P, seed):
-    """Each way the shuffles run gives the oracle's rows bit for bit: a thread
-    per row in shared memory (n = 1,000, 4,000 rows: 27 rows to a block), a
-    warp per row in shared memory (n = 30,000: 7 uint8 rows or 1 int32 row to
-    a block; n = 100,000 uint8: 1 row), in place in HBM (n = 60,000 with 4,000
-    rows, more than eight times what the warp path holds at once; n = 100,000
-    int32, where not one row fits).  In the last case row 80's stream has a
-    rejection at draw 5,503, the last of a 128-draw buffer of the warp path,
-    whose second draw lies past the buffer (found by a search over rows; the
-    first draw is checked here)."""
+    """Each way the shuffles run gives the oracle's rows bit for bit: in
+    shared memory with one row to a warp (n = 1,000, 4,000 rows: 27 rows to a
+    block; n = 30,000: 7 uint8 rows or 1 int32 row; n = 100,000 uint8: 1
+    row), two rows to a warp (n = 4,000, 9,999 uint8 rows: 33 to a block) and
+    four (n = 3,000, 9,999 uint8 rows: 66 to a block); in place in HBM (n =
+    60,000 with 4,000 rows, more than eight times what shared memory holds at
+    once; n = 100,000 int32, where not one row fits).  In the last case row
+    80's stream has a rejection at draw 5,503, the last of a 128-draw refill
+    of a row alone in its warp, whose second draw lies past the refill (found
+    by a search over rows; the first draw is checked here)."""
     obs = synth.observed_labels([n // 3, n // 3, n - 2 * (n // 3)], seed)
     if seed == 424242:
         x = oracle.philox4x32_10([5503 // 4, 0, 80, 0], [seed & 0xFFFFFFFF, seed >> 32])[5503 % 4]

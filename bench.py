@@ -344,7 +344,8 @@ def forms_compare(pk: dict, reps: int = 3) -> dict:
 
 
 def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
-                seed: int = 5005, burst_tests: int = 600) -> dict:
+                seed: int = 5005, burst_tests: int = 600, sweep: tuple = (30.0, 120.0, 160.0),
+                sweep_duration: float = 6.0, sweep_warmup_s: float = 1.5) -> dict:
     """Serving workload: 64 resident matrices (n log-uniform in 500..30,000,
     Gaussian points in R^16/R^32, Euclidean fp32), each with 1-20 categorical
     factors (K uniform in 2..12, Dirichlet(2) sizes, each group >= 2), tests of
@@ -352,9 +353,11 @@ def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
     ``rate`` tests/s, served with prepared matrices (each matrix's operands
     made on its first request).  Arrivals during the first ``warmup_s`` seconds are
     served but not counted; tests/s and p50/p99 latency (arrival to result)
-    are taken over the ``duration`` seconds after that.  Then ``burst_tests``
-    tests of the same mix are submitted at once: completed tests / time to the
-    last result is the server's capacity."""
+    are taken over the ``duration`` seconds after that.  The same server then
+    takes the offered rates in ``sweep`` (shorter phases, each drained before
+    the next) to show where p99 turns up.  Then ``burst_tests`` tests of the
+    same mix are submitted at once: completed tests / time to the last result
+    is the server's capacity."""
     import torch
     import paper_2505_04556_gb300 as pm
     from paper_2505_04556_gb300.serve import Request, Server
@@ -376,36 +379,52 @@ def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
     torch.cuda.synchronize()
     resident = sum(int(D.numel()) * 4 for D in mats.values())
     srv = Server(mats, n_slots=slots, reserve_per_slot=8 << 30, prepare=True)
-    reqs, measured = [], []
-    t0 = time.perf_counter()
-    t_next = t0
     k = 0
-    while True:
-        t_next += rng.exponential(1.0 / rate)
-        if t_next - t0 > warmup_s + duration:
-            break
-        while time.perf_counter() < t_next:
-            time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+
+    def draw():
         m = int(rng.integers(64))
         lab, K = factors[m][int(rng.integers(len(factors[m])))]
         P = 999 if rng.random() < 0.5 else 9999
-        r = srv.submit(Request(m, lab, K, P, seed=10_000 + k))
-        reqs.append(r)
-        if t_next - t0 >= warmup_s:
-            measured.append(r)
-        k += 1
-    for r in reqs:
-        r.done.wait(600)
-    t_meas = t0 + warmup_s
-    wall = max(r.t_done for r in measured) - t_meas
+        return m, lab, K, P
+
+    def phase(rate_, warm, dur):
+        """Poisson arrivals at rate_ for warm + dur seconds; the arrivals after
+        the warm-up are measured; waits for every result."""
+        nonlocal k
+        reqs, measured = [], []
+        t0 = time.perf_counter()
+        t_next = t0
+        while True:
+            t_next += rng.exponential(1.0 / rate_)
+            if t_next - t0 > warm + dur:
+                break
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+            m, lab, K, P = draw()
+            r = srv.submit(Request(m, lab, K, P, seed=10_000 + k))
+            reqs.append(r)
+            if t_next - t0 >= warm:
+                measured.append(r)
+            k += 1
+        for r in reqs:
+            r.done.wait(600)
+        wall = max(r.t_done for r in measured) - (t0 + warm)
+        return measured, wall
+
+    measured, wall = phase(rate, warmup_s, duration)
+    sweep_out = []
+    for rt in sweep:
+        meas_r, wall_r = phase(rt, sweep_warmup_s, sweep_duration)
+        sr = Server.summarize(meas_r, wall_r)
+        sweep_out.append({"offered_rate": rt, "tests_per_s": sr.get("tests_per_s"), "p50_s": sr.get("p50_s"),
+                          "p99_s": sr.get("p99_s"), "tests": sr.get("tests"),
+                          "mean_batch": sr.get("mean_batch")})
     # capacity: a burst of tests from the same mix submitted at once, timed
     # from the first submission to the last result (the server saturated)
     burst = []
     tb = time.perf_counter()
     for j in range(burst_tests):
-        m = int(rng.integers(64))
-        lab, K = factors[m][int(rng.integers(len(factors[m])))]
-        P = 999 if rng.random() < 0.5 else 9999
+        m, lab, K, P = draw()
         burst.append(srv.submit(Request(m, lab, K, P, seed=50_000 + j)))
     for r in burst:
         r.done.wait(600)
@@ -420,6 +439,7 @@ def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
            "tests": s.get("tests"), "errors": s.get("errors"), "offered_rate": rate,
            "duration_s": duration, "warmup_s": warmup_s, "slots": slots,
            "mean_batch": s.get("mean_batch"), "pair_perm_evals_per_s": evals / wall,
+           "sweep": sweep_out,
            "capacity_tests_per_s": burst_ok / burst_wall, "capacity_burst": burst_tests,
            "capacity_mean_batch": float(np.mean([r.batch_size for r in burst])),
            "matrices_resident": len(mats), "resident_gb": round(resident / 1e9, 1),
@@ -436,7 +456,8 @@ def serving_bench(args) -> None:
     import torch
     line = serving_run(args.rate, args.duration, args.slots)
     line.update({"higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-                 "gpu": torch.cuda.get_device_name(0)})
+                 "gpu": torch.cuda.get_device_name(0),
+                 "gpu_sms": torch.cuda.get_device_properties(0).multi_processor_count})
     print(json.dumps(line), flush=True)
 
 
@@ -736,7 +757,8 @@ def main():
                 "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "prepared": prepared, "serving": serving, "forms": forms,
                 "clocks": clocks,
                 "gpu_launches": int(prof["kernel_launches"]),
-                "gpu": torch.cuda.get_device_name(dev)}
+                "gpu": torch.cuda.get_device_name(dev),
+                "gpu_sms": torch.cuda.get_device_properties(dev).multi_processor_count}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

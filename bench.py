@@ -290,31 +290,35 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
-def forms_compare(pk: dict, reps: int = 3) -> dict:
-    """Every kernel form on one workload in the same run: euclid-20k (n =
-    20,000, K = 4), 4,000 label rows (512 for the brute force, which re-reads
-    D from HBM per row), the dominant kernel timed with CUDA events inside the
-    library (mean of ``reps`` launches after one warm-up; D is 1.6 GB, larger
-    than L2), each form's roofline fraction, and its largest relative error
-    against the FP64 oracle on 8 rows every form computes."""
+def forms_compare(pk: dict, reps: int = 3, workload: str = "euclid-20k", cases=None,
+                  idx=(0, 1, 63, 127, 255, 256, 300, 511)) -> dict:
+    """Kernel forms on one workload in the same run (default euclid-20k, n =
+    20,000, K = 4: every form, 4,000 label rows, 512 for the brute force,
+    which re-reads D from HBM per row), the dominant kernel timed with CUDA
+    events inside the library (mean of ``reps`` launches after one warm-up;
+    D is larger than L2), each form's roofline fraction, and its relative
+    errors against the FP64 oracle on the label rows ``idx`` every form
+    computes (largest, and mean signed)."""
     import torch
     import oracle
     import paper_2505_04556_gb300 as pm
-    cfg = synth.recipe("euclid-20k")
+    if cases is None:
+        cases = [("brute", dict(form=pm.FORM_BRUTE), 512),
+                 ("permblock_pair", dict(form=pm.FORM_PERMBLOCK, permblock_variant=0), 4000),
+                 ("permblock_f32", dict(form=pm.FORM_PERMBLOCK, permblock_variant=1), 4000),
+                 ("gemm", dict(form=pm.FORM_GEMM), 4000)]
+    cfg = synth.recipe(workload)
     n, K = cfg["n"], cfg["K"]
     X = synth.recipe_points(cfg)
     D = synth.recipe_matrix_device(cfg, X)
-    lab = synth.device_label_rows(cfg["labels"], 4000, cfg["seed_perms"], dtype=torch.uint8)
+    n_rows = max(rows for _, _, rows in cases)
+    lab = synth.device_label_rows(cfg["labels"], n_rows, cfg["seed_perms"], dtype=torch.uint8)
     w = torch.from_numpy(cfg["w"]).cuda()
-    idx = np.array([0, 1, 63, 127, 255, 256, 300, 511])
-    ref = oracle.sW_alg1(D.cpu().numpy(), lab[idx].cpu().numpy().astype(np.int32), K,
+    idx = np.array(idx)
+    ref = oracle.sW_alg1(D.cpu().numpy(), lab[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.int32), K,
                          cfg["w"].astype(np.float64))
     pairs = n * (n - 1) / 2
-    out = {"workload": "euclid-20k", "n": n, "K": K, "error_rows": idx.tolist()}
-    cases = [("brute", dict(form=pm.FORM_BRUTE), 512),
-             ("permblock_pair", dict(form=pm.FORM_PERMBLOCK, permblock_variant=0), 4000),
-             ("permblock_f32", dict(form=pm.FORM_PERMBLOCK, permblock_variant=1), 4000),
-             ("gemm", dict(form=pm.FORM_GEMM), 4000)]
+    out = {"workload": workload, "n": n, "K": K, "error_rows": idx.tolist()}
     with pm.Context(0) as ctx:
         for name, plan, rows in cases:
             pm.permanova_set_plan(ctx.handle, **plan)
@@ -331,16 +335,29 @@ def forms_compare(pk: dict, reps: int = 3) -> dict:
             evals = pairs * rows
             rl = roofline("gemm" if name == "gemm" else "permblock" if name.startswith("permblock")
                           else "brute", K, evals, ms, pk, None)
-            got = res.cpu().numpy()[idx]
+            rel = (res.cpu().numpy()[idx] - ref) / ref
             out[name] = {"evals_per_s": evals / (ms / 1e3), "kernel_ms": ms, "rows": rows,
                          "roofline_frac": rl["frac"], "bound": rl["bound"],
-                         "max_rel_err_vs_oracle": float(np.max(np.abs(got - ref) / ref))}
+                         "max_rel_err_vs_oracle": float(np.max(np.abs(rel))),
+                         "mean_rel_err_vs_oracle": float(np.mean(rel))}
         pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
-    out["gemm_over_best_fp32"] = out["gemm"]["evals_per_s"] / max(
-        out["permblock_pair"]["evals_per_s"], out["permblock_f32"]["evals_per_s"])
+    fp32 = [out[c]["evals_per_s"] for c in ("permblock_pair", "permblock_f32") if c in out]
+    out["gemm_over_best_fp32"] = out["gemm"]["evals_per_s"] / max(fp32)
     del D, lab
     torch.cuda.empty_cache()
     return out
+
+
+def precision_compare(pk: dict) -> dict:
+    """The precision configuration: braycurtis-50k (n = 50,000 Bray-Curtis
+    distances in [0, 1], K = 8): the split-BF16 tensor-core form against the
+    plain FP32 CUDA-core kernel on the same 4,000 label rows, each with its
+    errors against the FP64 oracle on eight rows spread over the launch."""
+    import paper_2505_04556_gb300 as pm
+    cases = [("permblock_pair", dict(form=pm.FORM_PERMBLOCK, permblock_variant=0), 4000),
+             ("gemm", dict(form=pm.FORM_GEMM), 4000)]
+    return forms_compare(pk, reps=2, workload="braycurtis-50k", cases=cases,
+                         idx=(0, 1, 127, 128, 255, 1000, 2047, 3999))
 
 
 def serving_run(rate: float, duration: float, slots: int, warmup_s: float = 3.0,
@@ -724,7 +741,7 @@ def main():
 
     cpu = None
     rows_h = lab[:64].cpu().numpy()
-    serving = forms = None
+    serving = forms = precision = None
     if rank == 0 and world == 1 and not args.no_serving:
         # the serving workload on the same GPU, after the step's buffers and the
         # context's scratch are given back
@@ -734,6 +751,7 @@ def main():
         torch.cuda.empty_cache()
         serving = serving_run(args.rate, args.duration, args.slots)
         forms = forms_compare(peaks())
+        precision = precision_compare(peaks())
     if rank == 0 and not args.no_cpu:
         cpu = oracle_rate(cfg, X, rows_h, 15.0)
 
@@ -755,6 +773,7 @@ def main():
                                   "L2 flushed between steps (2 x L2 write, untimed)"),
                            "parallelism": f"replicas x{world} (label rows split)"},
                 "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "prepared": prepared, "serving": serving, "forms": forms,
+                "precision": precision,
                 "clocks": clocks,
                 "gpu_launches": int(prof["kernel_launches"]),
                 "gpu": torch.cuda.get_device_name(dev),

@@ -70,8 +70,9 @@ typedef enum {
  *              once per label row (HBM-bound).
  *   PERMBLOCK  a triangle tile of D^2 is held in shared memory and reused by
  *              a block of 256 label rows, two per thread compared at once
- *              with packed FP16 equality (uint8 codes; 128 rows with FP32
- *              compares for uint16 codes), CUDA-core and issue-bound; the row
+ *              with packed FP16 equality (uint8 codes, and uint16 codes up to
+ *              2,048 groups; beyond that 128 rows with FP32 compares),
+ *              CUDA-core and issue-bound; the row
  *              weight is applied once per row segment as in Algorithm 2.
  *   GEMM       the dense-contraction form Z_p = (D o D) X_p with one-hot
  *              indicator columns X_p, on the tcgen05 tensor cores: D^2, scaled

@@ -188,11 +188,12 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
 }
 
 // ---------------------------------------------------------------------------
-// Paired variant (uint8 codes): each thread evaluates TWO label rows p and p'
-// (p' = p + 128) at once.  Its 64 column labels of both rows are held as FP16
-// pairs (0x43Lp, 0x43Lp': distinct finite values for the 256 byte values), and
-// one packed FP16 equality test against the row key (0x43g_p(i), 0x43g_p'(i))
-// sets two predicates, which gate two FP32 adds of the same d^2:
+// Paired variant (uint8 or uint16 codes): each thread evaluates TWO label rows
+// p and p' (p' = p + 128) at once.  Its 64 column labels of both rows are held
+// as FP16 pairs (uint8 code L as the pattern 0x43LL, uint16 code L < 2048 as
+// 0x4000 + L: distinct finite normal values either way), and one packed FP16
+// equality test against the row key (the pattern pair of g_p(i), g_p'(i)) sets
+// two predicates, which gate two FP32 adds of the same d^2:
 //   setp.eq.f16x2  P|Q, cl[j], key     (one compare for two evaluations)
 //   @P add.f32     acc_p,  acc_p,  d2
 //   @Q add.f32     acc_p', acc_p', d2
@@ -206,9 +207,64 @@ k_sw_permblock(const float* __restrict__ mat, uint32_t n, uint64_t ld, const L* 
 // ---------------------------------------------------------------------------
 constexpr int PB2_THREADS = 128;              // threads per CTA
 constexpr int PB2_ROWS = 2 * PB2_THREADS;     // label rows per CTA
-constexpr uint32_t PB2_LAB_BYTES = PB_T * PB2_THREADS * 2;   // row labels of p and p': 16 KB
 constexpr uint32_t PB2_WTAB = 2048;                          // FP32 weights staged per CTA (8 KB)
-constexpr uint32_t pb2_smem_bytes() { return PB_D2_BYTES + PB2_LAB_BYTES + PB2_WTAB * 4; }
+
+// The codes of the paired kernel: a row entry holds a row's codes for p and
+// p' (uint8: 8 bits each, uint16: 16 bits each), key() makes their FP16
+// pattern pair, cols() the pattern pairs of 64 columns from 16-byte loads.
+template <typename L> struct PairCodes;
+template <> struct PairCodes<uint8_t> {
+    using Row = uint16_t;
+    static __device__ __forceinline__ Row pack(uint32_t la, uint32_t lb) { return (Row)(la | (lb << 8)); }
+    static __device__ __forceinline__ uint32_t key(uint32_t row) { return __byte_perm(row, 0x43u, 0x4140); }
+    static __device__ __forceinline__ uint32_t la(uint32_t row) { return row & 0xFFu; }
+    static __device__ __forceinline__ uint32_t lb(uint32_t row) { return row >> 8; }
+    static __device__ __forceinline__ uint32_t col(uint32_t a, uint32_t b) { return 0x43004300u | a | (b << 16); }
+    static __device__ __forceinline__ void cols(const uint8_t* ga, const uint8_t* gb, uint32_t (&cl)[PB_T]) {
+        const uint4* sa = reinterpret_cast<const uint4*>(ga);
+        const uint4* sb = reinterpret_cast<const uint4*>(gb);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint4 va = __ldg(sa + h), vb = __ldg(sb + h);
+            const uint32_t xa[4] = {va.x, va.y, va.z, va.w}, xb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t lo = __byte_perm(xa[t], xb[t], 0x5140);   // a0 b0 a1 b1
+                const uint32_t hi = __byte_perm(xa[t], xb[t], 0x7362);   // a2 b2 a3 b3
+                cl[16 * h + 4 * t + 0] = __byte_perm(lo, 0x43u, 0x4140);
+                cl[16 * h + 4 * t + 1] = __byte_perm(lo, 0x43u, 0x4342);
+                cl[16 * h + 4 * t + 2] = __byte_perm(hi, 0x43u, 0x4140);
+                cl[16 * h + 4 * t + 3] = __byte_perm(hi, 0x43u, 0x4342);
+            }
+        }
+    }
+};
+template <> struct PairCodes<uint16_t> {
+    using Row = uint32_t;
+    static __device__ __forceinline__ Row pack(uint32_t la, uint32_t lb) { return la | (lb << 16); }
+    static __device__ __forceinline__ uint32_t key(uint32_t row) { return row + 0x40004000u; }
+    static __device__ __forceinline__ uint32_t la(uint32_t row) { return row & 0xFFFFu; }
+    static __device__ __forceinline__ uint32_t lb(uint32_t row) { return row >> 16; }
+    static __device__ __forceinline__ uint32_t col(uint32_t a, uint32_t b) { return 0x40004000u + (a | (b << 16)); }
+    static __device__ __forceinline__ void cols(const uint16_t* ga, const uint16_t* gb, uint32_t (&cl)[PB_T]) {
+        const uint4* sa = reinterpret_cast<const uint4*>(ga);
+        const uint4* sb = reinterpret_cast<const uint4*>(gb);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const uint4 va = __ldg(sa + h), vb = __ldg(sb + h);
+            const uint32_t xa[4] = {va.x, va.y, va.z, va.w}, xb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                cl[8 * h + 2 * t + 0] = __byte_perm(xa[t], xb[t], 0x5410) + 0x40004000u;   // a0 b0
+                cl[8 * h + 2 * t + 1] = __byte_perm(xa[t], xb[t], 0x7632) + 0x40004000u;   // a1 b1
+            }
+        }
+    }
+};
+template <typename L>
+constexpr uint32_t pb2_smem_bytes() {
+    return PB_D2_BYTES + PB_T * PB2_THREADS * (uint32_t)sizeof(typename PairCodes<L>::Row) + PB2_WTAB * 4;
+}
 
 // acc0 += d where the low FP16 halves of a and b are equal, acc1 += d where
 // the high halves are.
@@ -219,15 +275,18 @@ __device__ __forceinline__ void pair_add(float& acc0, float& acc1, uint32_t a, u
         : "r"(a), "r"(b), "f"(d));
 }
 
-template <bool VEC, int MINB>
+template <typename L, bool VEC, int MINB>
 __global__ void __launch_bounds__(PB2_THREADS, MINB)
 k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
-                    const uint8_t* __restrict__ labels, uint64_t lstride, uint64_t P, const WeightMap wm,
+                    const L* __restrict__ labels, uint64_t lstride, uint64_t P, const WeightMap wm,
                     uint32_t K, uint32_t n_pblocks, double* __restrict__ partials,
                     const DevStatus* __restrict__ st) {
+    using C = PairCodes<L>;
+    using Row = typename C::Row;
+    constexpr uint32_t LAB_BYTES = PB_T * PB2_THREADS * (uint32_t)sizeof(Row);   // row codes of p and p'
     extern __shared__ __align__(16) uint8_t pb_smem[];
     float (*d2)[PB_T] = reinterpret_cast<float (*)[PB_T]>(pb_smem);
-    uint16_t (*lrow)[PB2_THREADS] = reinterpret_cast<uint16_t (*)[PB2_THREADS]>(pb_smem + PB_D2_BYTES);
+    Row (*lrow)[PB2_THREADS] = reinterpret_cast<Row (*)[PB2_THREADS]>(pb_smem + PB_D2_BYTES);
     const uint32_t band = blockIdx.x / n_pblocks;
     const uint32_t q = blockIdx.x % n_pblocks;
     const uint64_t pa = (uint64_t)q * PB2_ROWS + threadIdx.x, pb = pa + PB2_THREADS;
@@ -239,10 +298,10 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
     }
     // inactive label rows mirror the last row so every load stays in bounds
     const uint64_t ra = act_a ? pa : P - 1, rb = act_b ? pb : P - 1;
-    const uint8_t* ga = labels + ra * lstride;
-    const uint8_t* gb = labels + rb * lstride;
+    const L* ga = labels + ra * lstride;
+    const L* gb = labels + rb * lstride;
     // the weight sets of the CTA's label rows as an FP32 table in shared memory
-    float* wtab = reinterpret_cast<float*>(pb_smem + PB_D2_BYTES + PB2_LAB_BYTES);
+    float* wtab = reinterpret_cast<float*>(pb_smem + PB_D2_BYTES + LAB_BYTES);
     const uint64_t p_first = (uint64_t)q * PB2_ROWS, p_last = min(P, p_first + PB2_ROWS) - 1;
     const uint64_t set_lo = wm.set_of(p_first);
     const uint64_t n_sets_cta = wm.set_of(p_last) - set_lo + 1;
@@ -256,7 +315,7 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
     const uint32_t rows = min((uint32_t)PB_T, n - 1 - r0);  // row n-1 has no pairs
     for (uint32_t r = 0; r < rows; ++r) {
         const uint32_t la = min((uint32_t)ga[r0 + r], K - 1), lb = min((uint32_t)gb[r0 + r], K - 1);
-        lrow[r][threadIdx.x] = (uint16_t)(la | (lb << 8));
+        lrow[r][threadIdx.x] = C::pack(la, lb);
     }
     double tot_a = 0.0, tot_b = 0.0;
 
@@ -288,28 +347,13 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
         // its d^2 is 0)
         uint32_t cl[PB_T];
         if (j0 + PB_T <= n) {
-            const uint4* sa = reinterpret_cast<const uint4*>(ga + j0);
-            const uint4* sb = reinterpret_cast<const uint4*>(gb + j0);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const uint4 va = __ldg(sa + h), vb = __ldg(sb + h);
-                const uint32_t xa[4] = {va.x, va.y, va.z, va.w}, xb[4] = {vb.x, vb.y, vb.z, vb.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const uint32_t lo = __byte_perm(xa[t], xb[t], 0x5140);   // a0 b0 a1 b1
-                    const uint32_t hi = __byte_perm(xa[t], xb[t], 0x7362);   // a2 b2 a3 b3
-                    cl[16 * h + 4 * t + 0] = __byte_perm(lo, 0x43u, 0x4140);
-                    cl[16 * h + 4 * t + 1] = __byte_perm(lo, 0x43u, 0x4342);
-                    cl[16 * h + 4 * t + 2] = __byte_perm(hi, 0x43u, 0x4140);
-                    cl[16 * h + 4 * t + 3] = __byte_perm(hi, 0x43u, 0x4342);
-                }
-            }
+            C::cols(ga + j0, gb + j0, cl);
         } else {
 #pragma unroll
             for (int c = 0; c < PB_T; ++c) {
                 const uint32_t j = j0 + c;
                 const uint32_t a = j < n ? ga[j] : 0u, b = j < n ? gb[j] : 0u;
-                cl[c] = 0x43004300u | a | (b << 16);
+                cl[c] = C::col(a, b);
             }
         }
         __syncthreads();
@@ -320,7 +364,7 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
 #pragma unroll 2
             for (uint32_t r = rg; r < rend; ++r) {
                 const uint32_t lab = lrow[r][threadIdx.x];
-                const uint32_t key = __byte_perm(lab, 0x43u, 0x4140);     // (0x43 la, 0x43 lb)
+                const uint32_t key = C::key(lab);     // the FP16 patterns of la and lb
                 const float4* drow = reinterpret_cast<const float4*>(&d2[r][0]);
                 float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll
@@ -333,8 +377,8 @@ k_sw_permblock_pair(const float* __restrict__ mat, uint32_t n, uint64_t ld,
                 }
                 // each row segment weighted once (Algorithm 2)
                 float w_a, w_b;
-                asm("ld.shared.f32 %0, [%1];" : "=f"(w_a) : "r"(wsa + ((lab & 0xFFu) << 2)));
-                asm("ld.shared.f32 %0, [%1];" : "=f"(w_b) : "r"(wsb + ((lab >> 8) << 2)));
+                asm("ld.shared.f32 %0, [%1];" : "=f"(w_a) : "r"(wsa + (C::la(lab) << 2)));
+                asm("ld.shared.f32 %0, [%1];" : "=f"(w_b) : "r"(wsb + (C::lb(lab) << 2)));
                 grp_a = fmaf(a0 + a1, w_a, grp_a);
                 grp_b = fmaf(b0 + b1, w_b, grp_b);
             }
@@ -376,7 +420,7 @@ static cudaError_t launch_pb_t(const SWProblem& pr, uint64_t lstride, double* pa
 // minb: CTAs per SM the register budget is sized for (3: 168 registers a
 // thread, the default, measured 0.87-0.91 of the issue roofline at n = 20k;
 // 4: 128 registers, more warps but spills, 0.81-0.86)
-template <int MINB>
+template <typename L, int MINB>
 static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double* partials,
                                   const DevStatus* st, cudaStream_t s) {
     const bool vec = (pr.ld % 4 == 0) && ((uintptr_t)pr.mat % 16 == 0);
@@ -384,20 +428,20 @@ static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double*
     const uint64_t n_pblocks = (pr.P + PB2_ROWS - 1) / PB2_ROWS;
     const uint64_t blocks = (uint64_t)n_bands * n_pblocks;
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    const uint32_t smem = pb2_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock_pair<true, MINB>,
+    const uint32_t smem = pb2_smem_bytes<L>();
+    cudaError_t e = cudaFuncSetAttribute(k_sw_permblock_pair<L, true, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sw_permblock_pair<false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(k_sw_permblock_pair<L, false, MINB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (vec)
-        k_sw_permblock_pair<true, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
-            pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
+        k_sw_permblock_pair<L, true, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     else
-        k_sw_permblock_pair<false, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
-            pr.mat, pr.n, pr.ld, (const uint8_t*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
+        k_sw_permblock_pair<L, false, MINB><<<(unsigned)blocks, PB2_THREADS, smem, s>>>(
+            pr.mat, pr.n, pr.ld, (const L*)pr.labels, lstride, pr.P, pr.weights(), pr.K,
             (uint32_t)n_pblocks, partials, st);
     return launched(1);
 }
@@ -405,23 +449,26 @@ static cudaError_t launch_pb_pair(const SWProblem& pr, uint64_t lstride, double*
 // pr.labels must be uint8 (pr.label_type == LABEL_U8) or uint16 codes with a
 // row stride of lstride elements, lstride * sizeof(code) a multiple of 16 and
 // the base address 16-byte aligned.  variant 0: the paired FP16-compare
-// kernel for uint8 codes whose weight sets fit its FP32 table (else, and for
-// uint16 codes, the FP32 compare-and-set kernel), sized for 3 CTAs per SM;
+// kernel for codes whose weight sets fit its FP32 table (at most 2,048
+// weights, so K <= 2,048 and the uint16 patterns 0x4000 + L stay normal FP16
+// values), sized for 3 CTAs per SM, else the FP32 compare-and-set kernel;
 // variant 2: the same paired kernel sized for 4 CTAs per SM; variant 1: the
 // FP32 compare-and-set kernel.
 cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
                                       const DevStatus* st, cudaStream_t s, int variant) {
+    // weight sets a CTA of the paired kernel can meet: one, a run of equal
+    // sets, or (ragged sets) at most all of them
+    const WeightMap wm = pr.weights();
+    const uint64_t sets = wm.row_start ? wm.n_sets
+                          : wm.set_rows ? (PB2_ROWS + wm.set_rows - 1) / wm.set_rows + 1 : 1;
+    const bool fits = sets * pr.K <= PB2_WTAB;
     if (pr.label_type == LABEL_U8) {
-        // weight sets a CTA of the paired kernel can meet: one, a run of equal
-        // sets, or (ragged sets) at most all of them
-        const WeightMap wm = pr.weights();
-        const uint64_t sets = wm.row_start ? wm.n_sets
-                              : wm.set_rows ? (PB2_ROWS + wm.set_rows - 1) / wm.set_rows + 1 : 1;
-        const bool fits = sets * pr.K <= PB2_WTAB;
-        if (fits && variant == 0) return launch_pb_pair<3>(pr, lstride, partials, st, s);
-        if (fits && variant == 2) return launch_pb_pair<4>(pr, lstride, partials, st, s);
+        if (fits && variant == 0) return launch_pb_pair<uint8_t, 3>(pr, lstride, partials, st, s);
+        if (fits && variant == 2) return launch_pb_pair<uint8_t, 4>(pr, lstride, partials, st, s);
         return launch_pb_t<uint8_t>(pr, lstride, partials, st, s);
     }
+    if (fits && variant == 0) return launch_pb_pair<uint16_t, 3>(pr, lstride, partials, st, s);
+    if (fits && variant == 2) return launch_pb_pair<uint16_t, 4>(pr, lstride, partials, st, s);
     return launch_pb_t<uint16_t>(pr, lstride, partials, st, s);
 }
 

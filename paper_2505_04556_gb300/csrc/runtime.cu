@@ -706,7 +706,7 @@ int permanova_autotune(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_
         cands.push_back(pl);
     }
     for (int var : {0, 2, 1}) {
-        if (var != 1 && K > 256) continue;
+        if (var != 1 && K > 2048) continue;   // the paired kernel holds up to 2,048 weights
         Plan pl = plan_of_form(PERMANOVA_FORM_PERMBLOCK);
         pl.pb_variant = var;
         cands.push_back(pl);

@@ -106,7 +106,8 @@ def test_label_types_and_padded_stride(ctx, form, ltype):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("K,ltype", [(255, pm.LABEL_U8), (256, pm.LABEL_U8), (300, pm.LABEL_U16)])
+@pytest.mark.parametrize("K,ltype", [(255, pm.LABEL_U8), (256, pm.LABEL_U8), (300, pm.LABEL_U16),
+                                     (2048, pm.LABEL_U16), (2049, pm.LABEL_U16)])
 def test_many_groups(ctx, form, K, ltype):
     if form == pm.FORM_GEMM and K > 256:
         pytest.skip("GEMM form holds at most 256 groups")
@@ -118,6 +119,30 @@ def test_many_groups(ctx, form, K, ltype):
     ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
     got = _run_sW(ctx, D, rows, K, w, form, ltype)
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-12)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("K", [257, 1000, 2048])
+def test_permblock_uint16_codes(ctx, variant, K):
+    """More than 256 groups: int32 labels become uint16 codes, which the paired
+    perm-block kernel (variants 0 and 2, FP16 patterns 0x4000 + L) and the
+    FP32 kernel (variant 1) both take; ragged tiles (n = 1,001) and a ragged
+    last block of label rows (300 rows)."""
+    rng = np.random.default_rng(K + variant)
+    n, P = 1001, 300
+    D = synth.euclidean_matrix(rng.standard_normal((n, 6)))
+    rows = rng.integers(0, K, size=(P, n)).astype(np.int32)
+    rows[0, :] = K - 1                       # the largest code in every column of one row
+    w = rng.uniform(0.01, 1.0, K).astype(np.float32)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    out = torch.empty(P, dtype=torch.float64, device="cuda")
+    pm.permanova_set_plan(ctx.handle, form=pm.FORM_PERMBLOCK, permblock_variant=variant)
+    try:
+        pm.permanova_sW(ctx.handle, _dev(D), n, n, _dev(rows), pm.LABEL_I32, K, P, _dev(w), out)
+        pm.permanova_sync(ctx.handle)
+    finally:
+        pm.permanova_set_plan(ctx.handle, pm.FORM_AUTO)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL, atol=1e-12)
 
 
 @pytest.mark.parametrize("form", FORMS + [pytest.param(pm.FORM_AUTO, id="auto")])

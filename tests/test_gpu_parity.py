@@ -367,6 +367,32 @@ def test_permanova_test_matches_oracle(ctx, n, K, P, seed):
     assert res["n_perms"] == P
 
 
+@pytest.mark.parametrize("form", FORMS[:2] + [pytest.param(pm.FORM_AUTO, id="auto")])
+def test_permanova_test_many_groups(ctx, form):
+    """The permutation test with more than 256 groups: the device permutations
+    are uint16 codes and the s_W pass takes them (brute force, the paired
+    perm-block kernel, the planner's choice); s_W of every row, s_T and the
+    count against the oracle."""
+    n, K, P, seed = 2003, 300, 199, 31
+    rng = np.random.default_rng(seed)
+    D = synth.euclidean_matrix(rng.standard_normal((n, 5)))
+    obs = np.concatenate([np.arange(K), rng.integers(0, K, n - K)]).astype(np.int32)
+    rng.shuffle(obs)
+    ref = oracle.permanova_test(D, obs, K, P, seed)
+    out_sW = torch.empty(P + 1, dtype=torch.float64, device="cuda")
+    ctx.set_form(form)
+    try:
+        res = pm.permanova_test(ctx.handle, _dev(D), n, n, _dev(obs), K, P, seed, out_sW)
+    finally:
+        ctx.set_form(pm.FORM_AUTO)
+    np.testing.assert_allclose(out_sW.cpu().numpy(), ref["s_W"], rtol=RTOL)
+    assert abs(res["s_T"] - ref["s_T"]) <= RTOL * ref["s_T"]
+    band = np.abs(ref["s_W"][1:] - ref["s_W"][0]) <= RTOL * ref["s_W"][0]
+    if not band.any():
+        assert res["n_ge"] == ref["n_ge"]
+        assert res["p_value"] == ref["p_value"]
+
+
 def test_invalid_label_reported(ctx):
     D, rows, w = _case(100, 3, 5, seed=1)
     rows = rows.copy()

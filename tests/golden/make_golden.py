@@ -40,17 +40,20 @@ def main():
     obs37, D16, lab16, rows16, D60, lab60 = golden_inputs()
     perms = oracle.permutations(obs37, 20, 9013)
     with open(os.path.join(HERE, "permutations_n37.txt"), "w") as f:
-        f.write("# oracle.permutations(observed, 20, seed=9013); row 0 = observed\n")
+        f.write("# Sec. 1 permutation test (labels reassigned at random): "
+                "oracle.permutations(observed, 20, seed=9013); row 0 = observed\n")
         for r in perms:
             f.write(" ".join(str(int(x)) for x in r) + "\n")
     sW = oracle.sW_alg1(D16, rows16, 3, synth.inv_sizes(lab16, 3).astype(np.float64))
     with open(os.path.join(HERE, "sW_integer_n16.txt"), "w") as f:
-        f.write("# oracle.sW_alg1 on synth.integer_matrix(16, 15, 7), 6 label rows; exact\n")
+        f.write("# Sec. 2, Algorithm 1 (s_W): oracle.sW_alg1 on synth.integer_matrix(16, 15, 7), "
+                "6 label rows; exact\n")
         for v in sW:
             f.write(float(v).hex() + "\n")
     res = oracle.permanova_test(D60, lab60, 2, 99, 31)
     with open(os.path.join(HERE, "test_euclid_n60.txt"), "w") as f:
-        f.write("# oracle.permanova_test(D60, labels, K=2, P=99, seed=31)\n")
+        f.write("# Sec. 1 permutation test with Sec. 2's s_W: "
+                "oracle.permanova_test(D60, labels, K=2, P=99, seed=31)\n")
         f.write(f"s_T {float(res['s_T']).hex()}\n")
         f.write(f"s_W_obs {float(res['s_W'][0]).hex()}\n")
         f.write(f"F_obs {float(res['F'][0]).hex()}\n")

@@ -655,8 +655,11 @@ template <typename L, typename Rows, int RPW>
 static cudaError_t launch_warp_path(uint32_t n, uint32_t ns, uint64_t total, const int32_t* g, L* out,
                                     Rows map, uint32_t rows, cudaStream_t s) {
     const size_t smem = (size_t)rows * (4 * fy_words(RPW) + (size_t)ns * sizeof(L));
+    // the kernel's shared-memory limit is one value for every launch (a call
+    // that set its own size could race with another thread's launch of a
+    // larger block and make that launch fail); smem <= FY_SMEM_MAX by plan
     cudaError_t e = cudaFuncSetAttribute(k_shuffle_warp<L, Rows, RPW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FY_SMEM_MAX);
     if (e != cudaSuccess) return e;
     const uint64_t blocks = (total + rows - 1) / rows;
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;

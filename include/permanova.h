@@ -237,10 +237,13 @@ int permanova_sW_host(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uin
  * allocation (and forbids others), and processes confined to a fixed device
  * memory pool with no headroom, where a new allocation would fail or evict
  * the host framework's own buffers.
- * It needs no context and allocates nothing: it runs the brute-force kernels
- * with their scratch (FP64 partial sums, FP64 weights, the device error word)
- * in one fixed 8 MiB device array that the library keeps resident on every
- * GPU that loads it, until the process exits.
+ * It needs no context and allocates nothing: it runs the perm-block kernel
+ * (when the labels are uint8 or uint16 codes whose rows start on 16-byte
+ * boundaries and its partials, one row of n_perms doubles per 64-row band,
+ * fit) or else the brute-force kernel, with their scratch (FP64 partial
+ * sums, FP64 weights, the device error word) in one fixed 8 MiB device array
+ * that the library keeps resident on every GPU that loads it, until the
+ * process exits.
  *   Arguments as permanova_sW (DEVICE mat, groupings, inv_group_sizes,
  *   out_sW; the current CUDA device is used).
  *   Limits: n_perms * 8 bytes must fit in the array after the error word and

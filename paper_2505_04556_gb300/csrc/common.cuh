@@ -159,8 +159,9 @@ cudaError_t launch_sumsq_triangle(const float* mat, uint32_t n, uint64_t ld, uin
 // perm-block CUDA-core form: partials is permblock_bands(n) x P; labels are
 // uint8/uint16 codes with a 16-byte-multiple row stride of lstride elements
 uint32_t permblock_bands(uint32_t n);
-// variant 0: the paired FP16-compare kernel for uint8 codes (default);
-// variant 1: the FP32 compare-and-set kernel
+// variant 0: the paired FP16-compare kernel for uint8 and uint16 codes (default);
+// variant 2: the same sized for 4 CTAs per SM; variant 1: the FP32
+// compare-and-set kernel
 cudaError_t launch_permblock_internal(const SWProblem& pr, uint64_t lstride, double* partials,
                                       const DevStatus* st, cudaStream_t s, int variant = 0);
 

@@ -4,9 +4,13 @@
 // every device allocation themselves (and forbid others), and processes that
 // run inside a fixed device-memory pool with no headroom, where a fresh
 // allocation would fail or evict the framework's own buffers.  For them,
-// permanova_sW_noalloc runs the brute-force s_W kernels with their scratch
-// (FP64 partial sums, FP64 weights, the device error word) in one fixed
-// file-scope device array instead of context memory.  It needs no context.
+// permanova_sW_noalloc runs an s_W kernel with its scratch (FP64 partial sums,
+// FP64 weights, the device error word) in one fixed file-scope device array
+// instead of context memory: the perm-block kernel (D tiles in shared memory
+// shared by 256 label rows, about ten times the brute force's rate) when the
+// labels are uint8 or uint16 codes whose rows start on 16-byte boundaries and
+// its partials (one row per 64-row band) fit the array, else the brute-force
+// kernel, whose partials shrink to fit.  It needs no context.
 //
 // The array is NOALLOC_BYTES (8 MiB) and stays resident on every GPU that
 // loads this library until the process exits.  All calls on a device share
@@ -147,14 +151,21 @@ extern "C" int permanova_sW_noalloc(const float* mat, uint32_t n, uint64_t ld, c
     DevStatus* st = reinterpret_cast<DevStatus*>(b + NOALLOC_STATUS);
     double* wd = reinterpret_cast<double*>(b + NOALLOC_W);
     double* partials = reinterpret_cast<double*>(b + part_off);
-    uint32_t chunks = brute_chunks(n, 0);
+    // the perm-block kernel reads the caller's codes in place (16-byte rows)
+    const uint64_t elem = label_type == LABEL_U8 ? 1 : label_type == LABEL_U16 ? 2 : 4;
+    const bool rows16 = elem <= 2 && ((uint64_t)n * elem) % 16 == 0 &&
+                        reinterpret_cast<uintptr_t>(groupings) % 16 == 0;
+    const uint32_t pb_bands = permblock_bands(n);
+    const bool permblock = rows16 && (uint64_t)pb_bands <= max_rows;
+    uint32_t chunks = permblock ? pb_bands : brute_chunks(n, 0);
     if ((uint64_t)chunks > max_rows) chunks = (uint32_t)max_rows;
 
     SWProblem pr{mat, n, ld, groupings, label_type, K, P, wd, out_sW};
     if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) == cudaSuccess &&
         (e = launch_widen(inv_group_sizes, K, wd, s)) == cudaSuccess &&
         (e = launch_validate_labels(groupings, label_type, (uint64_t)n * P, K, st, s)) == cudaSuccess &&
-        (e = launch_brute(pr, chunks, partials, st, s)) == cudaSuccess &&
+        (e = permblock ? launch_permblock_internal(pr, n, partials, st, s, 0)
+                       : launch_brute(pr, chunks, partials, st, s)) == cudaSuccess &&
         (e = launch_reduce_rows(partials, chunks, P, out_sW, s)) == cudaSuccess) {
         DevStatus h{};
         e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

@@ -2,7 +2,9 @@
 (plugins of frameworks that own every device allocation, processes confined
 to a fixed memory pool).  It runs with the library's fixed resident scratch
 array and must give the same s_W as permanova_sW and as the FP64 oracle, call
-after call, although every call reuses (and overwrites) the same array.
+after call, although every call reuses (and overwrites) the same array; rows
+of 1,024 and 2,048 uint8 labels take its perm-block kernel, the others its
+brute-force kernel.
 
 This file is collected last so that a failure here cannot hide any other
 test's result in a run that stops at the first failure.  It passes alone in a
@@ -44,7 +46,8 @@ def _case(n, K, P, seed):
     return D, rows, w
 
 
-@pytest.mark.parametrize("n,K,P,seed", [(1001, 4, 37, 1), (257, 3, 300, 2), (130, 7, 5, 4)])
+@pytest.mark.parametrize("n,K,P,seed", [(1001, 4, 37, 1), (257, 3, 300, 2), (130, 7, 5, 4),
+                                        (1024, 5, 600, 5), (2048, 3, 100, 6)])
 def test_noalloc_matches_permanova_sW_and_oracle_twice(ctx, n, K, P, seed):
     D, rows, w = _case(n, K, P, seed)
     ref_oracle = oracle.sW_alg1(D, rows, K, w.astype(np.float64))

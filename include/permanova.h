@@ -11,8 +11,8 @@
  *
  * over a dense distance matrix of which only the strict upper triangle
  * (column > row) is read; the diagonal and the lower triangle may hold
- * anything, NaN included.  Around it, permanova_test adds the steps the paper
- * places "before and after" s_W (Sec. 2) for the permutation test of Sec. 1:
+ * anything, NaN included.  Around it, permanova_test adds the steps that the
+ * paper leaves around s_W (Sec. 2) for the permutation test of Sec. 1:
  * group sizes, permutations of the observed grouping, the total sum of squares
  * s_T, the pseudo-F statistic and the permutation p-value.
  *

@@ -10,7 +10,7 @@ Functions and the passage each follows:
 * :func:`sW_alg1` -- Algorithm 1 (Sec. 2), FP64, OpenMP over permutations.
 * :func:`sW_alg2` -- Algorithm 2 (Sec. 2), the tiled variant, FP64.
 * :func:`sT` -- total sum of squares (1/n) sum_{i<j} d_ij^2 (textbook PERMANOVA,
-  the "steps before and after" s_W of Sec. 2).
+  the steps around s_W that Sec. 2 leaves out of its listings).
 * :func:`philox4x32_10`, :func:`permutations` -- the permutation test of Sec. 1:
   Philox4x32-10 (Salmon et al., SC'11) keyed by the seed, counter
   (block, 0, p, 0); Lemire's bounded draw; Fisher-Yates; row 0 = observed.

@@ -25,8 +25,8 @@
  *                    reference.
  *   oracle_sT        total sum of squares s_T = (1/n) sum_{i<j} d_ij^2, the
  *                    textbook PERMANOVA quantity (Sec. 1 refers to the method
- *                    [1-2]; the pre/post steps are described in Sec. 2 as
- *                    happening before and after s_W).
+ *                    [1-2]; Sec. 2 leaves these steps out of its listings as
+ *                    cheap ones around s_W).
  *   oracle_philox4x32_10, oracle_permutations
  *                    the permutation test of Sec. 1 (the objects' group
  *                    labels reassigned at random): permutation p >= 1 is an

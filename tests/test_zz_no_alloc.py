@@ -66,6 +66,25 @@ def test_noalloc_matches_permanova_sW_and_oracle_twice(ctx, n, K, P, seed):
         np.testing.assert_allclose(got, ref_oracle, rtol=RTOL)
 
 
+@pytest.mark.parametrize("n,K,P,seed", [(1024, 300, 50, 7), (1000, 9, 40, 8)])
+def test_noalloc_uint16_labels(ctx, n, K, P, seed):
+    """uint16 labels: rows of 1,024 (2,048 bytes) take the perm-block kernel,
+    rows of 1,000 (2,000 bytes, not a 16-byte multiple) the brute force;
+    both against the FP64 oracle, twice in a row."""
+    rng = np.random.default_rng(seed)
+    D = synth.euclidean_matrix(rng.standard_normal((n, 5)))
+    rows = rng.integers(0, K, size=(P, n)).astype(np.int32)
+    w = rng.uniform(0.01, 1.0, K).astype(np.float32)
+    ref = oracle.sW_alg1(D, rows, K, w.astype(np.float64))
+    Dd = torch.from_numpy(D).cuda()
+    lab = torch.from_numpy(rows.astype(np.uint16).view(np.int16)).cuda()
+    wd = torch.from_numpy(w).cuda()
+    for _ in range(2):
+        out = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
+        pm.permanova_sW_noalloc(Dd, n, n, lab, pm.LABEL_U16, K, P, wd, out)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL)
+
+
 def test_noalloc_rejects_oversized_calls(ctx):
     D, rows, w = _case(64, 2, 4, 3)
     out = torch.empty(4, dtype=torch.float64, device="cuda")

@@ -393,6 +393,34 @@ def test_permanova_test_many_groups(ctx, form):
         assert res["p_value"] == ref["p_value"]
 
 
+@pytest.mark.parametrize("form", FORMS + [pytest.param(pm.FORM_AUTO, id="auto")])
+@pytest.mark.parametrize("n,P", [(3, 1), (4, 2), (5, 7)])
+def test_permanova_test_smallest_cases(ctx, form, n, P):
+    """The smallest tests the method allows (n = 3 objects in two groups, one
+    permutation; then 4 and 5 objects): s_W of every row and s_T against the
+    oracle, and the exceedance count within the bounds the 1e-5 band around
+    the observed s_W allows."""
+    rng = np.random.default_rng(n * 10 + P)
+    A = rng.integers(1, 9, (n, n)).astype(np.float32)
+    D = np.triu(A, 1)
+    D = D + D.T
+    obs = np.array([0, 1] * n, dtype=np.int32)[:n]
+    ref = oracle.permanova_test(D, obs, 2, P, 77)
+    out_sW = torch.empty(P + 1, dtype=torch.float64, device="cuda")
+    ctx.set_form(form)
+    try:
+        res = pm.permanova_test(ctx.handle, _dev(D), n, n, _dev(obs), 2, P, 77, out_sW)
+    finally:
+        ctx.set_form(pm.FORM_AUTO)
+    np.testing.assert_allclose(out_sW.cpu().numpy(), ref["s_W"], rtol=RTOL)
+    assert abs(res["s_T"] - ref["s_T"]) <= 1e-12 * ref["s_T"]
+    obs_sW, perm_sW = ref["s_W"][0], ref["s_W"][1:]
+    lo = int(np.sum(perm_sW < obs_sW * (1 - RTOL)))
+    hi = int(np.sum(perm_sW <= obs_sW * (1 + RTOL)))
+    assert lo <= res["n_ge"] <= hi
+    assert res["n_perms"] == P
+
+
 def test_invalid_label_reported(ctx):
     D, rows, w = _case(100, 3, 5, seed=1)
     rows = rows.copy()

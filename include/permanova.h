@@ -119,8 +119,9 @@ int permanova_set_form(permanova_ctx *ctx, int form);
 /* A kernel plan: the form and its knobs (0 = the default of a knob). */
 typedef struct {
     int form;                     /* permanova_form_t; AUTO restores the planner */
-    int permblock_variant;        /* 0: paired FP16-compare kernel for uint8 codes (3 blocks/SM),
-                                     2: the same at 4 blocks/SM, 1: FP32 compare-and-set */
+    int permblock_variant;        /* 0: paired FP16-compare kernel for uint8 codes and uint16
+                                     codes up to 2,048 groups (3 blocks/SM), 2: the same at
+                                     4 blocks/SM, 1: FP32 compare-and-set */
     uint32_t gemm_rows_div;       /* tensor-core form: label rows per tile divided by 1, 2 or 4 */
     uint32_t gemm_drain_kblocks;  /* tensor-core form: k-blocks between FP64 drains, 1 .. 8 (default 8) */
     uint32_t brute_chunk_mult;    /* brute force: chunks per label row multiplied by 1 .. 16 */

@@ -45,11 +45,16 @@ L2_BYTES = 129 << 20
 
 
 def host_matrix_bytes(n: int, ld: int) -> int:
-    """Bytes of D that permanova_sW_host copies with the tensor-core form:
-    each 128-row band's flat host range, from its diagonal element to the end
-    of its last row (the band trapezoid s_W reads plus the rows' lower-left
-    parts, which come along in one flat copy)."""
-    return sum(((min(128, n - r0) - 1) * ld + n - r0) * 4 for r0 in range(0, n, 128))
+    """Bytes of D that permanova_sW_host copies with the tensor-core form: for
+    each 128-row band whose trapezoid rows span at least half the width, its
+    flat host range from the diagonal element to the end of its last row (the
+    rows' lower-left parts come along in one flat copy); for the later bands,
+    the trapezoid alone (one two-dimensional copy)."""
+    total = 0
+    for r0 in range(0, n, 128):
+        rows, width = min(128, n - r0), n - r0
+        total += (rows * width if 2 * width < n else (rows - 1) * ld + width) * 4
+    return total
 
 
 def peaks() -> dict:
@@ -753,7 +758,8 @@ def main():
                "clocks": e2e_clocks, "h2d_gbs": round(h2d_gbs, 1), "h2d_gbs_at_offsets": h2d_at,
                "timeline": timeline,
                "api": "permanova_sW_host (pinned host D, labels, weights, results; "
-                      "flat copies of D's bands in segments overlapped with the kernels)"}
+                      "band copies of D (flat, or 2D for the later bands) in segments overlapped "
+                      "with the kernels)"}
 
     cpu = None
     rows_h = lab[:64].cpu().numpy()

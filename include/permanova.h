@@ -214,10 +214,12 @@ int permanova_sW(permanova_ctx *ctx, const float *mat, uint32_t n_dims, uint64_t
 /* Same as permanova_sW with HOST buffers: mat (n_dims x ld fp32),
  * groupings, inv_group_sizes and out_sW live in host memory (pinned memory
  * gives full copy speed).  The call copies the inputs to the device, runs
- * s_W, copies the n_perms results back and synchronises `stream`.  All copies
- * are flat (one-dimensional).  With the tensor-core form each 128-row band b
- * is copied as the host range from element (128 b, 128 b) to the end of the
- * band's last row, in up to 16 segments (band counts ramping up 1 : 2 : 4 :
+ * s_W, copies the n_perms results back and synchronises `stream`.  With the
+ * tensor-core form each 128-row band b is copied as the flat host range from
+ * element (128 b, 128 b) to the end of the band's last row, or, when the
+ * band's rows span under half the width (n - 128 b < n / 2), as one
+ * two-dimensional copy of its trapezoid alone, in up to 16 segments (band
+ * counts ramping up 1 : 2 : 4 :
  * 8 : 8 : ..., so the kernels start after a short first copy) through three
  * device staging slots sized for the largest segment, and each segment's
  * kernels start as soon as it has landed, so the copies overlap the

@@ -849,6 +849,12 @@ int permanova_sync(permanova_ctx* ctx, void* stream) {
     return read_status(ctx, static_cast<cudaStream_t>(stream));
 }
 
+// Whether the host entry copies band I of an n-object matrix as a
+// two-dimensional copy of its trapezoid (rows 128 I .., columns 128 I .. n-1)
+// rather than as its flat host range: when the trapezoid's rows are under half
+// the matrix width.
+static bool host_band_2d(uint64_t n, uint64_t I) { return 2 * (n - 128 * I) < n; }
+
 int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t ld,
                       const void* groupings, int label_type, uint32_t K, uint64_t P, const float* w,
                       double* out, void* stream) {
@@ -861,15 +867,18 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
     SWLayout L;
     rc = layout_for(ctx, plan_for(ctx, n, K, P), n, ld, nullptr, label_type, K, P, &L);
     if (rc) return rc;
-    // Staging for the inputs and the output after the s_W scratch.  Only flat
-    // copies are used: two-dimensional copies out of some page-locked host
-    // buffers ran at a fraction of the flat rate (measured: 120 against
-    // 210 GB/s from the same torch-pinned buffer).  The tensor-core form reads D
-    // only through its band trapezoids: band I is the flat host range from
-    // element (128 I, 128 I) to the end of its last row (about 128 ld floats,
-    // the rows' lower-left parts included) and lands in the band-flat layout in
-    // one of kHostSlots staging slots; the prep kernel of its segment reads it
-    // there, so the device holds kHostSlots segments of D, not all of it.  The
+    // Staging for the inputs and the output after the s_W scratch.  The
+    // tensor-core form reads D only through its band trapezoids and gets them
+    // in the band-flat layout (band I = the host range from element (128 I,
+    // 128 I) to the end of its last row, row stride ld) in one of kHostSlots
+    // staging slots; the prep kernel of its segment reads it there, so the
+    // device holds kHostSlots segments of D, not all of it.  A band whose
+    // trapezoid is at least half its flat range comes in one flat copy (the
+    // rows' lower-left parts come along); a later band, whose rows are mostly
+    // left of the diagonal, comes in one two-dimensional copy of its
+    // trapezoid into the same layout (two-dimensional copies out of
+    // page-locked host memory ran at about 120 against 210 GB/s for flat
+    // ones, so they pay only where they move under half the bytes).  The
     // CUDA-core forms get the whole matrix in one flat copy (row stride ld).
     const bool gemm = L.form == PERMANOVA_FORM_GEMM;
     const uint32_t n_bands = (n + 127) / 128;
@@ -981,9 +990,17 @@ int permanova_sW_host(permanova_ctx* ctx, const float* mat, uint32_t n, uint64_t
             const uint64_t o0 = band_flat_offset(seg_band[k], ld, n);
             for (uint32_t I = seg_band[k]; I < seg_band[k + 1] && e == cudaSuccess; ++I) {
                 const uint64_t r0 = 128ull * I;
-                const size_t bytes = band_flat_floats(I, ld, n) * sizeof(float);
-                e = cudaMemcpyAsync(slot + (band_flat_offset(I, ld, n) - o0), mat + r0 * ld + r0, bytes,
-                                    cudaMemcpyHostToDevice, cs);
+                const uint64_t rows = std::min<uint64_t>(128, n - r0), width = n - r0;
+                float* dst = slot + (band_flat_offset(I, ld, n) - o0);
+                size_t bytes;
+                if (host_band_2d(n, I)) {
+                    bytes = rows * width * sizeof(float);
+                    e = cudaMemcpy2DAsync(dst, ld * sizeof(float), mat + r0 * ld + r0, ld * sizeof(float),
+                                          width * sizeof(float), rows, cudaMemcpyHostToDevice, cs);
+                } else {
+                    bytes = band_flat_floats(I, ld, n) * sizeof(float);
+                    e = cudaMemcpyAsync(dst, mat + r0 * ld + r0, bytes, cudaMemcpyHostToDevice, cs);
+                }
                 if (ctx->profiling) ctx->host_h2d_bytes += bytes;
             }
             if (e == cudaSuccess) e = cudaEventRecord(arr.seg_ready[k], cs);

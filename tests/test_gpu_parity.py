@@ -544,8 +544,10 @@ def test_host_entry_profile(ctx):
     finally:
         pm.permanova_profile_enable(ctx.handle, False)
         ctx.set_form(pm.FORM_AUTO)
-    # each band's flat host range: from (128 I, 128 I) to the end of its last row
-    bands = sum(((min(128, n - r0) - 1) * ld + n - r0) * 4 for r0 in range(0, n, 128))
+    # each band's flat host range, from (128 I, 128 I) to the end of its last
+    # row, or for a band whose rows span under half the width its trapezoid
+    bands = sum((min(128, n - r0) * (n - r0) if 2 * (n - r0) < n
+                 else (min(128, n - r0) - 1) * ld + n - r0) * 4 for r0 in range(0, n, 128))
     assert prof["host_calls"] == 1
     assert prof["host_h2d_bytes"] == bands + n * P + 4 * K
     assert 0.0 < prof["host_first_segment_ms"] <= prof["host_copy_ms"] <= prof["host_total_ms"]

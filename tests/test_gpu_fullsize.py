@@ -11,6 +11,9 @@ times (default kernel plan, uint8 label rows, the benchmark's batch sizes).
   the launch against Huygens' identity for Euclidean distances, s_W =
   sum_g sum_{i in g} |x_i - mu_g|^2 computed from the generating points in
   FP64 (a property that holds at any size).
+* the whole permutation test at n = 100,000 with 99,999 permutations in one
+  call: 256 rows against Huygens' identity, s_T against its closed form, the
+  count and p against the returned s_W values.
 """
 import numpy as np
 import pytest
@@ -108,3 +111,41 @@ def test_full_size_euclid_100k_huygens(ctx):
         closed = float(np.sum(np.bincount(g, weights=sq, minlength=K)) -
                        np.sum(np.einsum("kd,kd->k", sums, sums) / cnt))
         assert abs(got[r] - closed) <= RTOL * closed, (r, got[r], closed)
+
+
+def test_full_size_permanova_test_100k(ctx):
+    """The whole permutation test at the headline size in one permanova_test
+    call: n = 100,000, K = 10, 99,999 permutations (device permutations, the
+    s_W pass over all 100,000 label rows, s_T, F, the count).  s_W of 256 rows
+    spread over the 100,000 against Huygens' identity from the generating
+    points (the rows regenerated with permanova_permutations from the same
+    seed), s_T against its one-group closed form sum_i |x_i - mu|^2, and the
+    count and p against the returned s_W values."""
+    cfg = synth.recipe("euclid-100k")
+    X = synth.recipe_points(cfg)
+    D = synth.recipe_matrix_device(cfg, X)
+    n, K, P, seed = cfg["n"], cfg["K"], cfg["P"], 4321
+    obs = torch.from_numpy(np.ascontiguousarray(cfg["labels"], dtype=np.int32)).cuda()
+    out = torch.empty(P + 1, dtype=torch.float64, device="cuda")
+    res = pm.permanova_test(ctx.handle, D, n, n, obs, K, P, seed, out)
+    sW = out.cpu().numpy()
+    n_ge = int(np.sum(sW[1:] <= sW[0]))
+    assert res["n_perms"] == P
+    assert res["n_ge"] == n_ge and res["p_value"] == (1 + n_ge) / (1 + P)
+    mu = X.mean(axis=0)
+    s_T = float(np.sum((X - mu) ** 2))
+    assert abs(res["s_T"] - s_T) <= RTOL * s_T
+    del D
+    torch.cuda.empty_cache()
+    lab = torch.empty((P + 1, n), dtype=torch.uint8, device="cuda")
+    pm.permanova_permutations(ctx.handle, obs, n, K, P, seed, lab, pm.LABEL_U8)
+    torch.cuda.synchronize()
+    sq = np.einsum("ij,ij->i", X, X)
+    dim = X.shape[1]
+    for r in np.linspace(0, P, 256).astype(int):
+        g = lab[r].cpu().numpy().astype(np.int64)
+        cnt = np.bincount(g, minlength=K).astype(np.float64)
+        sums = np.stack([np.bincount(g, weights=X[:, d], minlength=K) for d in range(dim)], axis=1)
+        closed = float(np.sum(np.bincount(g, weights=sq, minlength=K)) -
+                       np.sum(np.einsum("kd,kd->k", sums, sums) / cnt))
+        assert abs(sW[r] - closed) <= RTOL * closed, (r, sW[r], closed)

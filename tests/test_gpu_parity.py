@@ -207,7 +207,7 @@ def test_constant_matrix_closed_form(ctx, form, n, K, c):
     """Every term equal is the worst case for accumulation order: each FP32
     rounding (and the tensor core's truncating accumulation) errs the same way.
     For d_ij = c off the diagonal, s_W[p] = c^2 sum_g w_g n_g (n_g - 1) / 2,
-    evaluated in FP64 from the label counts (Sec. 1's definition of s_W).
+    evaluated in FP64 from the label counts (s_W as Algorithm 1 defines it, Sec. 2).
     c = 1.0019550323486328 squares to 1 + 2^-8 + 2^-17, the worst value for a
     split of d^2 into two BF16 halves; c = 2.989486 was the worst constant for
     the tensor-core accumulation in a sweep of 60 values."""
@@ -229,7 +229,7 @@ def test_tight_clusters_far_apart(ctx, form):
     distances between clusters lie in [5, 12].  Each band's d^2 then spans
     ~2^37, and s_W of the observed labels (row 0) consists only of the equal
     tiny terms, so any rounding of them errs the same way for every pair:
-    s_W = eps^2 sum_g w_g n_g (n_g - 1) / 2 exactly (Sec. 1's definition).
+    s_W = eps^2 sum_g w_g n_g (n_g - 1) / 2 exactly (Algorithm 1's sum, Sec. 2).
     The permuted rows are checked against the oracle."""
     rng = np.random.default_rng(31)
     n, K = 1500, 3
@@ -254,7 +254,7 @@ def test_tight_clusters_far_apart(ctx, form):
 @pytest.mark.parametrize("scale", [1e-15, 1e15])
 def test_extreme_scales(ctx, form, scale):
     """D scaled by 1e-15 or 1e15 (d^2 from 1e-30 to 1e30, normal FP32): s_W
-    scales by scale^2 exactly (Sec. 1's definition is homogeneous of degree 2)."""
+    scales by scale^2 exactly (Algorithm 1's sum is homogeneous of degree 2 in D)."""
     D, rows, w = _case(900, 4, 40, seed=41)
     ref = oracle.sW_alg1(D, rows, 4, np.asarray(w, dtype=np.float64))
     got = _run_sW(ctx, (D.astype(np.float64) * scale).astype(np.float32), rows, 4, w, form)
